@@ -1,0 +1,356 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every check here compares the oracle with something other than itself: a
+dense state-vector or density-matrix simulation, a matrix exponential, a
+closed form, a count given by Burnside's lemma, the paper's printed example,
+or brute force over group elements.  No GPU is used.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import pp_inputs as pi
+from oracle import statevector as sv
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _single(oracle_lib, n, q_string, gates, noise_mode=0, p=0.0, eps=0.0, wmax=-1):
+    x, z = pi.to_masks([q_string], n)
+    st = oracle_lib.OracleState(n, x, z, np.array([1.0]), eps=eps, max_weight=wmax)
+    for s, th in gates:  # Heisenberg order: caller passes gates last-to-first
+        gx, gz = pi.to_masks([s], n)
+        st.apply_gate(gx[0], gz[0], th, noise_mode, p)
+    x, z, c = st.export()
+    return dict(zip(pi.from_masks(x, z, n), c))
+
+
+# ------------------------------------------------ single-gate closed forms
+# App. A / Prop. 1 proof, read with U = exp(-i theta P / 2):
+# U^dag Q U = cos(theta) Q + sin(theta) (i P Q) for anticommuting P, Q.
+
+@pytest.mark.parametrize("theta", [0.3, -1.1, 2.5])
+def test_rz_on_x(oracle_lib, theta):
+    out = _single(oracle_lib, 1, "X", [("Z", theta)])
+    assert out["X"] == pytest.approx(math.cos(theta), abs=1e-15)
+    assert out["Y"] == pytest.approx(-math.sin(theta), abs=1e-15)
+
+
+@pytest.mark.parametrize("theta", [0.3, -1.1, 2.5])
+def test_rx_on_z_and_y(oracle_lib, theta):
+    out = _single(oracle_lib, 1, "Z", [("X", theta)])
+    assert out["Z"] == pytest.approx(math.cos(theta), abs=1e-15)
+    assert out["Y"] == pytest.approx(math.sin(theta), abs=1e-15)
+    out = _single(oracle_lib, 1, "Y", [("X", theta)])
+    assert out["Y"] == pytest.approx(math.cos(theta), abs=1e-15)
+    assert out["Z"] == pytest.approx(-math.sin(theta), abs=1e-15)
+
+
+def test_commuting_gate_is_identity(oracle_lib):
+    out = _single(oracle_lib, 3, "ZZI", [("ZZZ", 0.7), ("XXI", 0.4)])
+    assert out == {"ZZI": 1.0}
+
+
+def test_random_rotations_match_matrix_conjugation(oracle_lib):
+    """Sign rule of i P Q for multi-qubit P, Q: compare with U^dag Q U built
+    from dense matrices and decomposed over all 4^n strings."""
+    rng = np.random.default_rng(7)
+    n = 3
+    for trial in range(40):
+        q = "".join(rng.choice(list("IXYZ"), size=n))
+        gates = []
+        for _ in range(3):
+            p = "".join(rng.choice(list("IXYZ"), size=n))
+            if p == "I" * n:
+                p = "X" + p[1:]
+            gates.append((p, float(rng.uniform(-3, 3))))
+        want = sv.heisenberg_decompose(n, gates, q)
+        got = _single(oracle_lib, n, q, list(reversed(gates)))
+        keys = set(want) | {k for k, v in got.items() if abs(v) > 1e-13}
+        for k in keys:
+            assert got.get(k, 0.0) == pytest.approx(want.get(k, 0.0), abs=1e-12), (q, gates, k)
+
+
+# ------------------------------------------------- state-vector checks
+
+def test_config0_heisenberg_matches_statevector(oracle_lib):
+    wl = pi.config0_heisenberg(n=8, dt=0.05, steps=3)
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    ref = sv.statevector_expectations(wl.circuit.layers, wl.observable.terms, wl.state.bloch)
+    np.testing.assert_allclose(vals, ref, atol=1e-10, rtol=0)
+
+
+def test_two_qubit_heisenberg_closed_form(oracle_lib):
+    """n = 2: H = XX + YY + ZZ = 2 SWAP - 1; from |01>, <Z_0>(t) = cos 4t.
+    The three rotations on one pair commute, so Trotter steps are exact."""
+    dt = 0.13
+    wl = pi.config0_heisenberg(n=2, dt=dt, steps=6)
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    want = [math.cos(4 * (k + 1) * dt) for k in range(6)]
+    np.testing.assert_allclose(vals, want, atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_circuit_matches_statevector(oracle_lib, seed):
+    n = 6
+    circ = pi.random_circuit(n, n_layers=3, gates_per_layer=8, seed=seed, max_support=4)
+    obs = pi.random_observable(n, 5, seed=seed + 100, max_weight=3)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    wl = pi.Workload("rand", circ, obs, pi.ProductState(n, v))
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    # run_workload applies the *last* layer first and reads <O> after each
+    # Heisenberg layer; the state vector reads after each time layer.  The
+    # k-th Heisenberg value is the expectation after layers L-k..L-1 in time.
+    L = len(circ.layers)
+    for k in range(L):
+        layers = circ.layers[L - 1 - k:]
+        ref = sv.statevector_expectations(layers, obs.terms, v)[-1]
+        assert vals[k] == pytest.approx(ref, abs=1e-10)
+
+
+# ------------------------------------------------------- noise pins
+
+def test_per_gate_noise_matches_density_matrix(oracle_lib):
+    n = 4
+    circ = pi.random_circuit(n, n_layers=2, gates_per_layer=6, seed=11, max_support=2)
+    obs = pi.random_observable(n, 4, seed=12, max_weight=2)
+    st = pi.random_product_state(n, 13)
+    wl = pi.Workload("noisy", circ, obs, st, noise_p=0.07, noise_mode=1)
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    ref = sv.density_expectations(n, circ.layers, obs.terms, st.bloch, p_gate=0.07)
+    assert vals[-1] == pytest.approx(ref[-1], abs=1e-12)
+
+
+def test_per_layer_noise_matches_density_matrix(oracle_lib):
+    n = 4
+    circ = pi.random_circuit(n, n_layers=3, gates_per_layer=5, seed=21, max_support=2)
+    obs = pi.random_observable(n, 4, seed=22, max_weight=3)
+    st = pi.random_product_state(n, 23)
+    wl = pi.Workload("noisy", circ, obs, st, noise_p=0.2, noise_mode=2)
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    ref = sv.density_expectations(n, circ.layers, obs.terms, st.bloch, gamma_layer=0.2)
+    assert vals[-1] == pytest.approx(ref[-1], abs=1e-12)
+
+
+# ------------------------------------------- orbit representatives
+
+def _all_strings(n):
+    return ["".join(t) for t in itertools.product("IXYZ", repeat=n)]
+
+
+def _necklaces(n):
+    return sum(4 ** math.gcd(j, n) for j in range(1, n + 1)) // n
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_zn_representative_count_is_necklace_number(oracle_lib, n):
+    """Burnside / Example B.2: |R^{Z_n}_n| = (1/n) sum_j 4^gcd(j, n)."""
+    strings = _all_strings(n)
+    x, z = pi.to_masks(strings, n)
+    ox, oz = oracle_lib.canonical(n, 1, x, z)
+    reps = {tuple(a) + tuple(b) for a, b in zip(ox.tolist(), oz.tolist())}
+    assert len(reps) == _necklaces(n)
+    if n == 3:
+        assert len(reps) == 24  # the paper's worked example
+    if n in (5, 7):  # prime n: (4^n + 4(n-1)) / n, Example 1
+        assert len(reps) == (4 ** n + 4 * (n - 1)) // n
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_sn_representative_count_is_tetrahedral(oracle_lib, n):
+    """Example B.3: |R^{S_n}_n| = C(n+3, 3)."""
+    strings = _all_strings(n)
+    x, z = pi.to_masks(strings, n)
+    ox, oz = oracle_lib.canonical(n, 2, x, z)
+    reps = {tuple(a) + tuple(b) for a, b in zip(ox.tolist(), oz.tolist())}
+    assert len(reps) == math.comb(n + 3, 3)
+
+
+def _int_value(s):
+    # Definition "Lowest integer representation": I,X,Y,Z -> 0,1,2,3; qubit q has weight 4^q
+    return sum("IXYZ".index(ch) * 4 ** q for q, ch in enumerate(s))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_sn_representative_is_argmin_over_all_permutations(oracle_lib, n):
+    """Algorithm 3 counts letters instead of enumerating n! permutations; the
+    result must equal the brute-force argmin of int() over every permutation."""
+    rng = np.random.default_rng(n)
+    strings = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(40)]
+    x, z = pi.to_masks(strings, n)
+    ox, oz = oracle_lib.canonical(n, 2, x, z)
+    got = pi.from_masks(ox, oz, n)
+    for s, g in zip(strings, got):
+        best = min(("".join(s[i] for i in perm) for perm in itertools.permutations(range(n))),
+                   key=_int_value)
+        assert g == best
+
+
+@pytest.mark.parametrize("n", [3, 5, 8])
+def test_zn_representative_is_argmin_and_invariant(oracle_lib, n):
+    rng = np.random.default_rng(100 + n)
+    strings = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(60)]
+    x, z = pi.to_masks(strings, n)
+    got = pi.from_masks(*oracle_lib.canonical(n, 1, x, z), n)
+    for s, g in zip(strings, got):
+        rots = [s[j:] + s[:j] for j in range(n)]
+        assert g == min(rots, key=_int_value)
+        # shifting the input does not change the representative
+        t = s[1:] + s[:1]
+        xt, zt = pi.to_masks([t], n)
+        assert pi.from_masks(*oracle_lib.canonical(n, 1, xt, zt), n)[0] == g
+
+
+def test_paper_z3_representatives_lie_in_distinct_orbits(oracle_lib):
+    with open(os.path.join(GOLDEN, "z3_representatives.txt")) as f:
+        listed = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(listed) == 24
+    x, z = pi.to_masks(listed, 3)
+    reps = pi.from_masks(*oracle_lib.canonical(3, 1, x, z), 3)
+    assert len(set(reps)) == 24
+
+
+# ---------------------------------------------- Theorem 1 and observations
+
+def _symmetric_sn_layer(n, a, b, c):
+    """exp(-i a sum_{i<j} ZZ / 2) (commuting, so exactly S_n-invariant), then
+    RX(b) and RZ(c) on every qubit."""
+    gates = [(pi.pauli(n, {i: "Z", j: "Z"}), a) for i in range(n) for j in range(i + 1, n)]
+    gates += [(pi.pauli(n, {i: "X"}), b) for i in range(n)]
+    gates += [(pi.pauli(n, {i: "Z"}), c) for i in range(n)]
+    return gates
+
+
+@pytest.mark.parametrize("state", ["zero", "neel"])
+def test_theorem1_zn_merge_is_exact_on_ring(oracle_lib, state):
+    n = 6
+    wl = pi.config1_ring(n=n, steps=3, eps=0.0, max_weight=-1)
+    wl.state = pi.zero_state(n) if state == "zero" else pi.neel_state(n)
+    plain_st, plain = oracle_lib.run_workload(wl, group=0, record_each_step=True)
+    merged_st, merged = oracle_lib.run_workload(wl, group=1, record_each_step=True)
+    np.testing.assert_allclose(merged, plain, atol=1e-12, rtol=0)
+    ref = sv.statevector_expectations(wl.circuit.layers, wl.observable.terms, wl.state.bloch)
+    np.testing.assert_allclose(plain, ref, atol=1e-10, rtol=0)
+    assert len(merged_st) < len(plain_st)
+
+
+@pytest.mark.parametrize("state", ["plus", "neel"])
+def test_theorem1_sn_merge_is_exact_on_symmetric_layer(oracle_lib, state):
+    n = 5
+    layer = _symmetric_sn_layer(n, 0.37, 0.81, -0.45)
+    circ = pi.Circuit(n, [list(layer) for _ in range(2)])
+    st = pi.plus_state(n) if state == "plus" else pi.neel_state(n)
+    wl = pi.Workload("sn", circ, pi.mean_z(n), st)
+    _, plain = oracle_lib.run_workload(wl, group=0, record_each_step=True)
+    merged_st, merged = oracle_lib.run_workload(wl, group=2, record_each_step=True)
+    np.testing.assert_allclose(merged, plain, atol=1e-12, rtol=0)
+    assert len(merged_st) <= math.comb(n + 3, 3)
+
+
+def test_observation1_orbit_supported_operator_is_unchanged(oracle_lib):
+    n = 5
+    rng = np.random.default_rng(5)
+    strings = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(30)]
+    x, z = pi.to_masks(strings, n)
+    reps = sorted(set(pi.from_masks(*oracle_lib.canonical(n, 1, x, z), n)))
+    xr, zr = pi.to_masks(reps, n)
+    coef = rng.normal(size=len(reps))
+    st = oracle_lib.OracleState(n, xr, zr, coef, group=1)
+    got = dict(zip(pi.from_masks(*st.export()[:2], n), st.export()[2]))
+    assert got == pytest.approx(dict(zip(reps, coef)))
+
+
+def test_observation2_merged_count_lower_bound(oracle_lib):
+    """1/|G| <= N~/N: the merged operator never has fewer than N/|G| terms."""
+    n = 6
+    wl = pi.config1_ring(n=n, steps=4, eps=0.0, max_weight=-1)
+    ox, oz, oc = wl.observable.arrays()
+    plain = oracle_lib.OracleState(n, ox, oz, oc, group=0)
+    for layer in range(4):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        plain.apply_layer(gx, gz, th, group=0)
+        x, z, c = plain.export()
+        merged = oracle_lib.OracleState(n, x, z, c, group=1)
+        assert len(merged) * n >= len(plain)
+        assert len(merged) <= len(plain)
+
+
+# ------------------------------------------------------ overlaps
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_sn_orbit_average_matches_permutation_bruteforce(oracle_lib, n):
+    st = pi.random_product_state(n, 31 + n)
+    strings = []
+    for nx in range(n + 1):
+        for ny in range(n + 1 - nx):
+            for nz in range(n + 1 - nx - ny):
+                strings.append("Z" * nz + "Y" * ny + "X" * nx + "I" * (n - nx - ny - nz))
+    x, z = pi.to_masks(strings, n)
+    got = oracle_lib.sym_overlap(n, 2, x, z, st.bloch)
+    for s, g in zip(strings, got):
+        vals = []
+        for perm in itertools.permutations(range(n)):
+            t = "".join(s[perm[q]] for q in range(n))
+            v = 1.0
+            for q, ch in enumerate(t):
+                if ch != "I":
+                    v *= st.bloch[q, "XYZ".index(ch)]
+            vals.append(v)
+        assert g == pytest.approx(float(np.mean(vals)), abs=1e-14)
+
+
+def test_sym_overlap_equals_plain_for_invariant_state(oracle_lib):
+    n = 6
+    rng = np.random.default_rng(3)
+    strings = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(50)]
+    x, z = pi.to_masks(strings, n)
+    for st in (pi.plus_state(n), pi.zero_state(n)):
+        plain = oracle_lib.sym_overlap(n, 0, x, z, st.bloch)
+        for g in (1, 2):
+            np.testing.assert_allclose(oracle_lib.sym_overlap(n, g, x, z, st.bloch), plain,
+                                       atol=1e-15)
+
+
+def test_total_spin_normalisation(oracle_lib):
+    """<+|S^2|+> = n(n+2)/4 (normalisation S_0^2 of Fig. 2)."""
+    for n in (4, 7, 36):
+        obs = pi.total_spin_squared(n)
+        x, z, c = obs.arrays()
+        st = oracle_lib.OracleState(n, x, z, c)
+        assert st.expect(pi.plus_state(n).bloch) == pytest.approx(n * (n + 2) / 4, rel=1e-14)
+
+
+# ------------------------------------------------------ truncation rules
+
+def test_truncation_threshold_and_weight(oracle_lib):
+    n = 4
+    strings = ["ZIII", "XXII", "YYYI", "ZZZZ"]
+    x, z = pi.to_masks(strings, n)
+    coef = np.array([1e-3, 1e-4, 0.5, 0.9])
+    st = oracle_lib.OracleState(n, x, z, coef, eps=1e-3, max_weight=3)
+    got = dict(zip(pi.from_masks(*st.export()[:2], n), st.export()[2]))
+    # |c| >= eps kept (ZIII at exactly eps), XXII below eps, ZZZZ too heavy
+    assert got == {"ZIII": 1e-3, "YYYI": 0.5}
+
+
+def test_truncation_never_drops_zero_when_off(oracle_lib):
+    n = 2
+    x, z = pi.to_masks(["ZI", "XI"], n)
+    st = oracle_lib.OracleState(n, x, z, np.array([0.0, 1.0]))
+    assert len(st) == 2
+
+
+def test_s2_invariant_for_symmetric_heisenberg_a2a(oracle_lib):
+    """S^2 commutes with each exp(-i dt (XX+YY+ZZ)) pair gate (Heisenberg
+    all-to-all, config 0 family), so <S^2> stays n(n+2)/4 from |+>^n."""
+    n = 5
+    wl = pi.config0_heisenberg(n=n, dt=0.07, steps=2)
+    wl.observable = pi.total_spin_squared(n)
+    wl.state = pi.plus_state(n)
+    _, vals = oracle_lib.run_workload(wl, record_each_step=True)
+    np.testing.assert_allclose(vals, [n * (n + 2) / 4] * 2, rtol=1e-12)
