@@ -1,0 +1,334 @@
+"""Benchmark: Pauli-term gate updates/s on the translation-symmetric ring.
+
+Workload (one "step" = one whole job): the n=32 ring circuit (RZZ(0.4) on
+all bonds, RX(0.6), RZ(0.3) on all qubits; 20 Trotter steps = 1920 gates),
+observable (1/n) sum Z_i, state |0...0>, coefficient truncation 1e-4, Pauli
+weight <= 10, FP64.  It is propagated twice, plain and Z_32-merged, and
+<O> is read for both.  One gate update = one (live term, gate) pair.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is measured with the observable
+already in device memory; ``e2e`` goes through the host-buffer C-ABI calls
+(pp_create from host arrays, pp_expect back to the host).  ``roofline`` is for
+the gate kernel, timed with CUDA events captured around every gate kernel on
+the context's stream during the timed steps.  ``cpu_baseline`` times the CPU
+oracle on a bounded prefix of the same workload.  With N > 1 (torchrun) every
+rank runs an independent replica of the job (the path does not shard).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pp_inputs as pi  # noqa: E402
+
+WORKLOAD = "ring_n32_20steps_eps1e-4_w10_plain+Z32"
+METRIC = "pauli_term_gate_updates_per_s"
+UNIT = "updates/s"
+KEY_BYTES = 16   # one uint64 X word + one uint64 Z word (n = 32)
+COEF_BYTES = 8   # FP64
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.lines = []
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+GROUPS = {"both": (0, 1), "plain": (0,), "zn": (1,)}
+
+
+def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, only="both"):
+    """One job: plain then Z_n-merged propagation of the whole circuit.
+    marks: optional [event, event, event] recorded before, between, after."""
+    n = wl.circuit.n
+    stats = []
+    vals = []
+    for gi, group in enumerate(GROUPS[only]):
+        if marks is not None:
+            marks[gi].record(stream)
+        cfg = pp.pp_config_default(n_qubits=n, symmetry=group, coeff_eps=wl.eps,
+                                   max_weight=wl.max_weight, cuda_stream=stream,
+                                   profile_kernels=int(profile))
+        if host_inputs:
+            ox, oz, oc = wl.observable.arrays()
+            ctx = pp.pp_create(cfg, ox, oz, oc)
+        else:
+            dx, dz, dc = obs_dev
+            ctx = pp.pp_create_device(cfg, len(wl.observable.terms), dx, dz, dc)
+        for packed, th in layers:
+            pp.pp_apply_layer(ctx, packed, th, True)
+        vals.append(pp.pp_expect(ctx, wl.state.bloch))
+        stats.append(pp.pp_stats(ctx))
+        pp.pp_destroy(ctx)
+    if marks is not None:
+        marks[2].record(stream)
+    return vals, stats
+
+
+def bench_ours(args):
+    import torch
+    import paper_2512_12094_gb300 as pp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pp.build()
+    pp.load()
+
+    wl = pi.config1_ring()
+    L = len(wl.circuit.layers)
+    layers = []
+    for layer in reversed(range(L)):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        layers.append((pp.pack_gates(gx, gz), th))
+    ox, oz, oc = wl.observable.arrays()
+    dev = torch.device("cuda", local)
+    obs_dev = (torch.from_numpy(ox.view(np.int64)).to(dev), torch.from_numpy(oz.view(np.int64)).to(dev),
+               torch.from_numpy(oc).to(dev))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_job(host_inputs, profile):
+        flush.zero_()
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        if args.only != "both":
+            ev[1] = ev[0]
+        vals, stats = run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=ev,
+                              only=args.only)
+        ev[2].synchronize()
+        return vals, stats, ev
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            run_job(pp, wl, layers, obs_dev, stream, False, False, only=args.only)
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms_total, upd, launches = 0.0, 0.0, 0
+        split = [0.0, 0.0]
+        vals = stats = None
+        for _ in range(args.steps):
+            vals, stats, ev = timed_job(False, args.profile_timed)
+            ms_total += ev[0].elapsed_time(ev[2])
+            if args.only == "both":
+                split[0] += ev[0].elapsed_time(ev[1])
+                split[1] += ev[1].elapsed_time(ev[2])
+            for st in stats:
+                upd += st["gate_updates"]
+                launches += st["kernel_launches"]
+        clk = clocks.stop()
+        barrier()
+        # end to end through the host-buffer API (inputs copied in, result read back)
+        e2e_ms = 0.0
+        if not args.no_e2e:
+            for _ in range(args.steps):
+                _, _, ev = timed_job(True, False)
+                e2e_ms += ev[0].elapsed_time(ev[2])
+        # roofline pass: the same job once more, every gate kernel bracketed
+        # by CUDA events on the context's stream
+        _, pstats, _ = timed_job(False, True)
+    ac = sum(st["anticommuting_terms"] for st in pstats)
+    pupd = sum(st["gate_updates"] for st in pstats)
+    gate_ms = sum(st["gate_kernel_ms"] for st in pstats)
+    gate_n = sum(st["gate_kernels_timed"] for st in pstats)
+
+    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    upd_per_rank = upd / args.steps
+    total_upd = upd_per_rank * world * args.steps
+    value = total_upd / (ms_max / 1e3)
+    e2e_value = total_upd / (e2e_max / 1e3) if e2e_max > 0 else None
+    hbm, peak_kind = peaks()
+    per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
+    bytes_alg = KEY_BYTES * pupd + per_ac * ac
+    achieved = bytes_alg / (gate_ms / 1e3) / 1e9 if gate_ms > 0 else None
+    gates_per_job = len(GROUPS[args.only]) * sum(len(l[1]) for l in layers)
+    h2d = len(GROUPS[args.only]) * (ox.nbytes + oz.nbytes + oc.nbytes + wl.state.bloch.nbytes +
+                                     sum(p.nbytes + th.nbytes for p, th in layers))
+    d2h = len(GROUPS[args.only]) * (8 + L * 512)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline(seconds=args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.only == "both" else WORKLOAD + ":" + args.only,
+                   "n_qubits": 32, "trotter_steps": 20, "gates_per_job": gates_per_job,
+                   "coeff_eps": 1e-4, "max_weight": 10, "updates_per_job": upd_per_rank,
+                   "l2": "flushed (256 MB write) before every timed job",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "breakdown_ms_per_step": {"plain": split[0] / args.steps, "zn": split[1] / args.steps,
+                                  "gate_kernels_profiled_job": gate_ms},
+        "result": {"expect": vals, "live_terms": [st["live_terms"] for st in stats]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "kernel": "gate_kernel<1>", "peak_kind": peak_kind,
+                     "bytes_model": "16 B key per live term + 64 B per live anticommuting term",
+                     "avg_launch_us": 1e3 * gate_ms / max(gate_n, 1),
+                     "algorithmic_bytes_per_launch": bytes_alg / max(gate_n, 1),
+                     "timing": "CUDA events around every gate kernel of one extra job"},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(seconds=20.0):
+    """The CPU oracle, as it stands, on a bounded prefix of the same workload:
+    plain and Z_32-merged propagation, layer by layer, each run stopped once
+    it has used seconds/2 of CPU time."""
+    import oracle
+    oracle.build()
+    wl = pi.config1_ring()
+    total_upd = 0.0
+    total_t = 0.0
+    done = []
+    for group in (0, 1):
+        ox, oz, oc = wl.observable.arrays()
+        st = oracle.OracleState(32, ox, oz, oc, group=group, eps=wl.eps, max_weight=wl.max_weight)
+        t0 = time.process_time()
+        k = 0
+        for layer in reversed(range(len(wl.circuit.layers))):
+            gx, gz, th = wl.circuit.gate_arrays(layer)
+            st.apply_layer(gx, gz, th, group=group)
+            k += 1
+            if time.process_time() - t0 > seconds / 2:
+                break
+        total_t += time.process_time() - t0
+        total_upd += st.updates
+        done.append(k)
+    return {"value": total_upd / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d (plain) and %d (Z_32) of 20 Trotter steps of the job, "
+                      "%.1f s CPU, %.3g updates" % (done[0], done[1], total_t, total_upd)}
+
+
+def bench_reference(args):
+    """The oracle as the reference arm, on the host cores (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(4.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=per)
+    vals = [cpu_baseline(seconds=per) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="also bracket every gate kernel with events inside the timed steps")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * pp.h -- C ABI of the GB300 symmetry-merging Pauli propagation library.
+ *
+ * The library evolves an observable O = sum_s c_s s, s a Pauli string over n
+ * qubits, backwards through a circuit of Pauli rotations (the Heisenberg
+ * picture of Appendix A), merges strings related by a symmetry group into
+ * orbit representatives (Algorithm 1, Eq. O-merging; Algorithms 2 and 3) and
+ * returns Tr[rho O_0] for a product state rho.  All per-term work runs in the
+ * library's CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pauli strings: W = ceil(n/64) words per mask, qubit q in word q/64, bit
+ *   q%64.  x bit set for X and Y, z bit set for Z and Y (the symplectic form
+ *   of Appendix E).  Arrays of strings are row-major [m][W].
+ * Gates: a gate is exp(-i theta P / 2).  For P anticommuting with Q the
+ *   conjugation is U^dag Q U = cos(theta) Q + sin(theta) (i P Q) (App. A,
+ *   Prop. 1 proof; the paper writes the angle without the factor 1/2).
+ * Orbit representatives: the lowest integer representation of Appendix E
+ *   with digits I=0, X=1, Y=2, Z=3 and qubit q carrying weight 4^q.
+ * Truncation (Sec. "Numerical examples", coefficient truncation): after every
+ *   gate and every merge a term is kept iff |c| >= coeff_eps (when
+ *   coeff_eps > 0) and its Pauli weight is <= max_weight (when >= 0).
+ * Errors: every call returns a pp_status; no C++ exception crosses the ABI.
+ *   pp_last_error() gives a message for the calling thread's last failure.
+ * Threads: a pp_ctx is used by one host thread at a time.
+ * Memory: host pointers passed in are read before the call returns and are
+ *   never retained.  Device memory of a context is owned by the context and
+ *   released by pp_destroy.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PP_OK = 0,
+  PP_ERR_ARG = 1,       /* invalid argument (sizes, null pointers, enum values) */
+  PP_ERR_OOM = 2,       /* a device allocation failed */
+  PP_ERR_CAPACITY = 3,  /* the term table would exceed mem_budget_bytes */
+  PP_ERR_SYMMETRY = 4,  /* layer, observable or state does not have the declared symmetry */
+  PP_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  PP_ERR_TIMEOUT = 6,   /* a bounded device wait ran out */
+  PP_ERR_BUSY = 7,      /* server queue full */
+  PP_ERR_REJECTED = 8,  /* job can never fit the server's memory budget */
+  PP_ERR_STATE = 9,     /* call not valid in the context's current state */
+  PP_ERR_INTERNAL = 10  /* device-side consistency check failed (hash probe bound) */
+} pp_status;
+
+typedef enum { PP_SYM_NONE = 0, PP_SYM_ZN = 1, PP_SYM_SN = 2 } pp_symmetry;
+typedef enum { PP_COEF_F64 = 0, PP_COEF_F32 = 1 } pp_coef_type;
+typedef enum { PP_NOISE_NONE = 0, PP_NOISE_PER_GATE = 1, PP_NOISE_PER_LAYER = 2 } pp_noise_mode;
+
+/* A Pauli rotation generator P: words [0, W) of x and z are used, the rest
+ * must be zero. */
+typedef struct {
+  uint64_t x[4];
+  uint64_t z[4];
+} pp_pauli;
+
+typedef struct {
+  int n_qubits;            /* 1..256 */
+  int symmetry;            /* pp_symmetry: group used by merges and overlaps */
+  int batch;               /* must be 1 (one angle set) */
+  int coef_type;           /* pp_coef_type; PP_COEF_F64 only */
+  double coeff_eps;        /* coefficient truncation threshold; 0 = off */
+  int max_weight;          /* Pauli-weight truncation; < 0 = off */
+  int noise_mode;          /* pp_noise_mode */
+  double noise_p;          /* per-gate: p of (1-p)^k damping; per-layer: gamma of exp(-gamma |Q|) */
+  size_t mem_budget_bytes; /* ceiling on the context's device memory; 0 = no ceiling */
+  void* cuda_stream;       /* cudaStream_t to run on; NULL = the context creates its own */
+  int check_symmetry;      /* nonzero: validate layers against the group (PP_ERR_SYMMETRY) */
+  int use_graphs;          /* nonzero: replay repeated layers from captured CUDA graphs */
+  int profile_kernels;     /* nonzero: bracket every kernel that applies gates with CUDA
+                              events on the context's stream and accumulate their
+                              durations into pp_stats_t.gate_kernel_ms */
+  int layer_kernel;        /* nonzero (default): all gates of a layer run in one persistent
+                              cooperative kernel with a grid barrier between gates; zero:
+                              one kernel per gate, replayed from CUDA graphs */
+} pp_config;
+
+typedef struct pp_ctx pp_ctx;
+
+typedef struct {
+  int64_t live_terms;      /* terms with a kept coefficient */
+  int64_t stored_terms;    /* table entries including truncated slots awaiting compaction */
+  int64_t capacity;        /* table capacity in terms */
+  double gate_updates;     /* sum over applied gates of the live terms entering the gate */
+  int64_t gates_applied;
+  int64_t merges;          /* symmetry or identical-string merges performed */
+  int64_t compactions;
+  int64_t regrows;
+  size_t device_bytes;     /* device memory currently held by the context */
+  double anticommuting_terms; /* sum over applied gates of live terms anticommuting with P */
+  int64_t kernel_launches; /* kernels launched by the context (graph nodes included) */
+  double gate_kernel_ms;   /* with profile_kernels: summed duration of the kernels that applied
+                              gates (one per layer, or one per gate without layer_kernel) */
+  int64_t gate_kernels_timed; /* number of launches summed in gate_kernel_ms */
+} pp_stats_t;
+
+/* Fill *cfg with defaults: n_qubits = 0 (must be set), no symmetry, batch 1,
+ * FP64, truncation off, no noise, no budget, own stream, checks and graphs on. */
+pp_status pp_config_default(pp_config* cfg);
+
+/* Create a context holding O = sum_i coef[i] s_i (Algorithm 1, step 1).
+ * x, z: host arrays [n_terms][W]; coef: host array [n_terms].  Duplicate
+ * strings accumulate.  With cfg->symmetry != PP_SYM_NONE the strings are
+ * mapped to their orbit representatives and merged, giving O~_L of Alg. 1.
+ * The truncation rules are then applied.  n_terms may be 0.
+ * Errors: PP_ERR_ARG (bad config, null pointers with n_terms > 0, string bits
+ * beyond n_qubits), PP_ERR_OOM, PP_ERR_CAPACITY, PP_ERR_CUDA. */
+pp_status pp_create(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
+                    const uint64_t* z, const double* coef, pp_ctx** out);
+
+/* As pp_create, but x, z and coef are device pointers (same layout) that
+ * stay owned by the caller and are only read, on the context's stream,
+ * before the call returns. */
+pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
+                           const uint64_t* z, const double* coef, pp_ctx** out);
+
+/* Release every device and host resource of ctx.  NULL is accepted. */
+pp_status pp_destroy(pp_ctx* ctx);
+
+/* One Heisenberg layer O_{l-1} = U_l^dag O~_l U_l (Algorithm 1, step 2a, and
+ * Appendix A).  gates[0..n_gates) and theta[0..n_gates) describe U_l in TIME
+ * order; they are applied from the last to the first.  Per gate: per-gate
+ * damping (noise_mode PER_GATE: c <- c (1-p)^k, k = non-identity sites of Q on
+ * the gate's support), conjugation, merge of identical strings, truncation.
+ * noise_mode PER_LAYER damps every term by exp(-p |Q|) once before the gates
+ * (the noise layer follows U_l in time).  With symmetric_boundary != 0 the
+ * layer ends with the symmetry merge of Eq. (O-merging) (Algorithm 2 for
+ * Z_n, Algorithm 3 for S_n) and another truncation.  Callers apply layers
+ * from the last (l = L) to the first (l = 1).
+ * Errors: PP_ERR_ARG; PP_ERR_SYMMETRY when check_symmetry is set and the gate
+ * multiset (with angles) is not mapped onto itself by the group generators;
+ * PP_ERR_CAPACITY when the table would exceed the budget -- the context then
+ * holds the state after the last completed gate and pp_stats reports it;
+ * PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_INTERNAL. */
+pp_status pp_apply_layer(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const double* theta,
+                         int symmetric_boundary);
+
+/* Replace every string by its orbit representative under the context's
+ * group (Algorithm 2 line "argmin int(T^j s)"; Algorithm 3 line "Z^{nZ}
+ * Y^{nY} X^{nX}") without accumulating: the table may then hold duplicates
+ * until pp_merge.  Any later call that needs unique strings merges first.
+ * Errors: PP_ERR_STATE when the context has no symmetry. */
+pp_status pp_canonicalize(pp_ctx* ctx);
+
+/* Accumulate identical strings (the merge step of Algorithms 2 and 3 and of
+ * standard PP), then apply the truncation rules.  Coefficient sums use FP64
+ * atomics, so their rounding order is not fixed. */
+pp_status pp_merge(pp_ctx* ctx);
+
+/* Drop every term with |c| < eps (eps > 0) or weight > max_weight (>= 0).
+ * Does not change the rules applied by later calls. */
+pp_status pp_truncate(pp_ctx* ctx, double eps, int max_weight);
+
+/* Tr[rho O] (Algorithm 1, step 3) for rho = prod_q (I + bx X + by Y + bz Z)/2,
+ * bloch = host array [n][3] of (bx, by, bz).  With a symmetry each
+ * representative r contributes c_r times the orbit average of Tr[rho g.r],
+ * which equals Tr[rho r] when rho is symmetric (Eq. 2) and keeps the result
+ * exact for a symmetric O when rho is not.  The sum is accumulated in FP64
+ * in a fixed order.  *out receives one double.
+ * Errors: PP_ERR_SYMMETRY when neither rho nor the ingested O is invariant. */
+pp_status pp_expect(pp_ctx* ctx, const double* bloch, double* out);
+
+/* Number of live terms and of stored table entries. */
+pp_status pp_num_terms(pp_ctx* ctx, int64_t* live, int64_t* stored);
+
+/* Copy the live terms to host arrays x, z [capacity][W] and coef
+ * [capacity]; *n_out receives the count.  PP_ERR_ARG if capacity is too
+ * small (nothing written; *n_out still receives the count). */
+pp_status pp_export(pp_ctx* ctx, int64_t capacity, uint64_t* x, uint64_t* z, double* coef,
+                    int64_t* n_out);
+
+/* Counters of the context (host copy, synchronises the stream). */
+pp_status pp_stats(pp_ctx* ctx, pp_stats_t* out);
+
+/* Raise or lower the memory budget of a context (0 = no ceiling). */
+pp_status pp_set_budget(pp_ctx* ctx, size_t mem_budget_bytes);
+
+/* Wait for all work queued by ctx. */
+pp_status pp_synchronize(pp_ctx* ctx);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* pp_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Stateless entry points on caller-owned device arrays.  Keys are device
+ * arrays [m][2W] with the x words of a string followed by its z words.  All
+ * work is queued on `stream` (cudaStream_t, NULL = default stream); the call
+ * returns once it is queued unless stated otherwise.
+ * ------------------------------------------------------------------------ */
+
+/* keys_out[i] = orbit representative of keys_in[i] (Algorithms 2 and 3).
+ * keys_out may equal keys_in. */
+pp_status pp_canonical_keys(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                            uint64_t* keys_out, void* stream);
+
+/* Accumulate identical strings of (keys_in, coef_in)[0..m) after mapping each
+ * to its representative under `symmetry` (PP_SYM_NONE: identity), i.e. the
+ * merge loop of Algorithms 2 and 3.  Writes the distinct strings and their
+ * FP64 sums to keys_out [m][2W], coef_out [m] in unspecified order and the
+ * count to *m_out (host pointer; the call synchronises the stream).  Uses a
+ * temporary device hash table obtained with cudaMallocAsync on `stream`. */
+pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                         const double* coef_in, uint64_t* keys_out, double* coef_out,
+                         int64_t* m_out, void* stream);
+
+/* *out (device pointer, one double) = sum_i coef[i] ov(keys[i]), ov the
+ * product-state overlap of pp_expect (orbit-averaged under `symmetry`),
+ * bloch a device array [n][3].  Deterministic two-pass FP64 reduction. */
+pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* keys,
+                         const double* coef, const double* bloch, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

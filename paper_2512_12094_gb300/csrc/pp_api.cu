@@ -1,0 +1,1133 @@
+// Host side of the C ABI declared in include/pp.h.
+//
+// A context owns two term tables of equal capacity (the live one and a
+// spare used as the destination of merges and compactions), a device
+// control block, and small constant tables.  Gates run as one kernel each;
+// repeated layers are replayed from captured CUDA graphs.  The host reads the
+// control block once per layer: a gate that finds less than twice its input
+// size free does nothing and raises `stall`; the host then grows the tables
+// and relaunches the layer from that gate (earlier gates skip themselves).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+#include "pp_internal.h"
+
+using namespace ppk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pp_status fail(pp_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+pp_status cuda_fail(cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(PP_ERR_OOM, msg);
+  return fail(PP_ERR_CUDA, msg);
+}
+
+#define PP_CUDA(call)                                    \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+  } while (0)
+
+#define PP_TRY(call)                   \
+  do {                                 \
+    pp_status _s = (call);             \
+    if (_s != PP_OK) return _s;        \
+  } while (0)
+
+uint64_t next_pow2(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+int popcount64(uint64_t v) { return __builtin_popcountll(v); }
+
+struct Buf {
+  uint64_t* keys = nullptr;
+  double* coef = nullptr;
+  uint64_t* index = nullptr;
+  uint64_t cap = 0;
+  uint64_t icap = 0;
+};
+
+struct ArgsEntry {
+  std::vector<unsigned char> sig;  // bytes of the gate arguments
+  GateArgs* d_args = nullptr;      // device copy
+  size_t n = 0;
+  uint64_t last_use = 0;
+};
+
+struct GraphEntry {
+  std::vector<unsigned char> sig;  // bytes of the gate arguments
+  int grid = 0;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+};
+
+size_t table_bytes(uint64_t cap, uint64_t icap, int W) {
+  return (size_t)cap * (16 * W + 8) + (size_t)icap * 8;
+}
+
+}  // namespace
+
+struct pp_ctx {
+  pp_config cfg{};
+  int n = 0, W = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 1;
+  int gate_bps = 4;   // resident gate-kernel blocks per SM
+  int layer_bps = 0;  // co-resident layer-kernel blocks per SM (0: no cooperative path)
+  std::vector<ArgsEntry> arg_cache;
+  cudaEvent_t ev_layer[2] = {nullptr, nullptr};
+  Buf buf[2];
+  int active = 0;
+  DevTable* d_desc = nullptr;  // [3]: table 0, table 1, active copy
+  DevCtl* d_ctl = nullptr;
+  DevCtl* h_ctl = nullptr;     // pinned mirror
+  double* d_damp = nullptr;    // (1-p)^k
+  double* d_ldamp = nullptr;   // exp(-gamma k)
+  double* d_partials = nullptr;
+  double* d_out = nullptr;
+  double* h_out = nullptr;     // pinned
+  double* d_bloch = nullptr;
+  double* d_sn = nullptr;      // S_n overlap table
+  double* d_sn_work = nullptr;
+  std::vector<double> sn_bloch;  // bloch vectors the S_n table was built for
+  uint64_t n_terms = 0;          // host mirror of DevCtl::n_terms
+  int64_t n_live = 0;
+  bool merged = true;
+  bool obs_invariant = false;
+  size_t bytes = 0;
+  int64_t merges = 0, compactions = 0, regrows = 0;
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  int overlap_grid = 0;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev_start, ev_end;  // per gate position (profile_kernels)
+  double gate_ms = 0.0;
+  int64_t gates_timed = 0;
+};
+
+namespace {
+
+pp_status dmalloc(pp_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  c->bytes += bytes;
+  return PP_OK;
+}
+
+void dfree(pp_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFreeAsync(p, c->stream);
+  c->bytes -= (bytes == 0 ? 16 : bytes);
+}
+
+// Index slots per dense entry of capacity: the index is a power of two of at
+// least 1.5x the capacity, so its load stays below 2/3 even when the table is
+// full (a gate stalls before that can happen) and is about 1/4 at a layer start.
+uint64_t index_cap_for(uint64_t cap) { return next_pow2(cap + cap / 2); }
+
+pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
+  b.cap = cap;
+  b.icap = index_cap_for(cap);
+  PP_TRY(dmalloc(c, (void**)&b.keys, (size_t)cap * 16 * c->W));
+  PP_TRY(dmalloc(c, (void**)&b.coef, (size_t)cap * 8));
+  PP_TRY(dmalloc(c, (void**)&b.index, (size_t)b.icap * 8));
+  PP_CUDA(cudaMemsetAsync(b.index, 0, (size_t)b.icap * 8, c->stream));
+  return PP_OK;
+}
+
+void free_buf(pp_ctx* c, Buf& b) {
+  dfree(c, b.keys, (size_t)b.cap * 16 * c->W);
+  dfree(c, b.coef, (size_t)b.cap * 8);
+  dfree(c, b.index, (size_t)b.icap * 8);
+  b = Buf();
+}
+
+DevTable desc_of(const Buf& b) {
+  DevTable t;
+  t.keys = b.keys;
+  t.coef = b.coef;
+  t.index = b.index;
+  t.cap = b.cap;
+  t.imask = b.icap - 1;
+  return t;
+}
+
+// Write the descriptors of both tables and the active copy (synchronous
+// copy from host memory; only called when a table is (re)allocated).
+pp_status publish_desc(pp_ctx* c) {
+  DevTable h[3] = {desc_of(c->buf[0]), desc_of(c->buf[1]), desc_of(c->buf[c->active])};
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  PP_CUDA(cudaMemcpy(c->d_desc, h, sizeof(h), cudaMemcpyHostToDevice));
+  return PP_OK;
+}
+
+// Make the active copy point at c->active (stream ordered, device to device).
+pp_status activate(pp_ctx* c, int which) {
+  c->active = which;
+  PP_CUDA(cudaMemcpyAsync(c->d_desc + 2, c->d_desc + which, sizeof(DevTable),
+                          cudaMemcpyDeviceToDevice, c->stream));
+  return PP_OK;
+}
+
+pp_status read_ctl(pp_ctx* c) {
+  PP_CUDA(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  return PP_OK;
+}
+
+pp_status check_device_error(pp_ctx* c) {
+  unsigned e = c->h_ctl->error;
+  if (!e) return PP_OK;
+  if (e & kErrTimeout) return fail(PP_ERR_TIMEOUT, "device wait for a published index slot ran out");
+  if (e & kErrAppend) return fail(PP_ERR_INTERNAL, "append past table capacity");
+  return fail(PP_ERR_INTERNAL, "hash index probe bound exhausted");
+}
+
+int grid_for(pp_ctx* c, uint64_t items, int per_thread) {
+  uint64_t want = (items + (uint64_t)kBlock * per_thread - 1) / ((uint64_t)kBlock * per_thread);
+  uint64_t maxg = (uint64_t)c->sms * 8;
+  if (want < 1) want = 1;
+  if (want > maxg) want = maxg;
+  return (int)want;
+}
+
+// Set n_next (append cursor) and n_live before a merge or compaction into
+// the spare table.
+pp_status ctl_prepare_insert(pp_ctx* c, unsigned long long first_free) {
+  unsigned long long nn = first_free;
+  long long live = 0;
+  PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_next, &nn, 8, cudaMemcpyHostToDevice, c->stream));
+  PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_live, &live, 8, cudaMemcpyHostToDevice, c->stream));
+  PP_CUDA(cudaStreamSynchronize(c->stream));  // the sources live on the host stack
+  return PP_OK;
+}
+
+// n_terms <- n_next (device to device) and read the control block back.
+pp_status ctl_commit(pp_ctx* c) {
+  PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_terms, &c->d_ctl->n_next, 8, cudaMemcpyDeviceToDevice,
+                          c->stream));
+  PP_TRY(read_ctl(c));
+  PP_TRY(check_device_error(c));
+  c->n_terms = c->h_ctl->n_terms;
+  c->n_live = c->h_ctl->n_live;
+  return PP_OK;
+}
+
+// Copy the kept entries of the active table into `dst` (fresh index) and make
+// it active.  extra_eps / extra_wmax implement pp_truncate.
+pp_status compact_into(pp_ctx* c, int dst, double extra_eps, int extra_wmax) {
+  Buf& d = c->buf[dst];
+  PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
+  PP_TRY(ctl_prepare_insert(c, 0));
+  PP_CUDA(launch_compact(c->W, grid_for(c, c->n_terms, 4), c->stream, desc_of(c->buf[c->active]),
+                         c->n_terms, desc_of(d), 1, c->cfg.coeff_eps, extra_eps, extra_wmax,
+                         c->d_ctl));
+  c->launches += 1;
+  PP_TRY(ctl_commit(c));
+  PP_TRY(activate(c, dst));
+  c->compactions++;
+  return PP_OK;
+}
+
+pp_status ensure_capacity(pp_ctx* c, uint64_t need) {
+  if (need <= c->buf[c->active].cap) return PP_OK;
+  uint64_t cap = std::max<uint64_t>(need, 1024);
+  cap = (cap + 1023) & ~1023ull;
+  size_t add = 2 * table_bytes(cap, index_cap_for(cap), c->W);
+  size_t keep = c->bytes - 2 * table_bytes(c->buf[0].cap, c->buf[0].icap, c->W);
+  if (c->cfg.mem_budget_bytes && keep + add > c->cfg.mem_budget_bytes)
+    return fail(PP_ERR_CAPACITY, "term table of capacity " + std::to_string(cap) +
+                                     " exceeds the memory budget");
+  int spare = 1 - c->active;
+  free_buf(c, c->buf[spare]);
+  PP_TRY(alloc_buf(c, c->buf[spare], cap));
+  PP_TRY(publish_desc(c));
+  PP_TRY(compact_into(c, spare, 0.0, -1));
+  int old = 1 - c->active;
+  free_buf(c, c->buf[old]);
+  PP_TRY(alloc_buf(c, c->buf[old], cap));
+  PP_TRY(publish_desc(c));
+  c->regrows++;
+  return PP_OK;
+}
+
+// Make room before (or in the middle of) a layer: drop truncated entries when
+// they are a quarter of the table or more, then make the capacity at least 4x
+// the entries, so that a stall (a gate needs room for twice its input) only
+// happens once a layer has doubled the table.  Every stall costs a host round
+// trip, a compaction and a relaunch, so growth is generous; untouched
+// capacity costs memory, not bandwidth.
+pp_status make_room(pp_ctx* c) {
+  if (c->cfg.coeff_eps > 0.0 && c->n_terms > 0 && 4 * (c->n_terms - c->n_live) >= c->n_terms)
+    PP_TRY(compact_into(c, 1 - c->active, 0.0, -1));
+  if (2 * c->n_terms <= c->buf[c->active].cap) return PP_OK;
+  return ensure_capacity(c, c->n_terms * 4);
+}
+
+// Accumulate the active table (after optional canonicalisation) into the
+// spare table and make it active: the merge of Algorithms 2 and 3.
+pp_status merge_active(pp_ctx* c, int group) {
+  int dst = 1 - c->active;
+  Buf& d = c->buf[dst];
+  Buf& s = c->buf[c->active];
+  PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
+  PP_TRY(ctl_prepare_insert(c, 0));
+  PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid_for(c, c->n_terms, 4), c->stream,
+                              s.keys, s.coef, c->n_terms, nullptr, c->cfg.coeff_eps > 0.0 ? 1 : 0,
+                              desc_of(d), c->d_ctl));
+  PP_CUDA(launch_finalize(grid_for(c, c->n_terms, 4), c->stream, desc_of(d), c->d_ctl,
+                          c->cfg.coeff_eps));
+  c->launches += 2;
+  PP_TRY(ctl_commit(c));
+  PP_TRY(activate(c, dst));
+  c->merged = true;
+  c->merges++;
+  return PP_OK;
+}
+
+bool key_has_bits_beyond(const uint64_t* x, const uint64_t* z, int n, int W) {
+  for (int j = 0; j < W; ++j) {
+    int lo = 64 * j;
+    uint64_t valid = (n >= lo + 64) ? ~0ull : ((n > lo) ? ((1ull << (n - lo)) - 1ull) : 0ull);
+    if ((x[j] | z[j]) & ~valid) return true;
+  }
+  return false;
+}
+
+// ---- symmetry generators on host-side strings (x words, z words) ----
+
+void get_bit(const uint64_t* m, int q, int& b) { b = (int)((m[q >> 6] >> (q & 63)) & 1ull); }
+
+void permute_string(const uint64_t* x, const uint64_t* z, int n, int W, const std::vector<int>& to,
+                    uint64_t* ox, uint64_t* oz) {
+  for (int j = 0; j < W; ++j) ox[j] = oz[j] = 0;
+  for (int q = 0; q < n; ++q) {
+    int xb, zb;
+    get_bit(x, q, xb);
+    get_bit(z, q, zb);
+    int t = to[q];
+    ox[t >> 6] |= (uint64_t)xb << (t & 63);
+    oz[t >> 6] |= (uint64_t)zb << (t & 63);
+  }
+}
+
+std::vector<std::vector<int>> generators(int group, int n) {
+  std::vector<std::vector<int>> gens;
+  if (n < 2 || group == PP_SYM_NONE) return gens;
+  std::vector<int> shift(n);
+  for (int q = 0; q < n; ++q) shift[q] = (q + n - 1) % n;  // T: qubit q -> q-1
+  gens.push_back(shift);
+  if (group == PP_SYM_SN) {
+    std::vector<int> swap01(n);
+    for (int q = 0; q < n; ++q) swap01[q] = q;
+    std::swap(swap01[0], swap01[1]);
+    gens.push_back(swap01);
+  }
+  return gens;
+}
+
+typedef std::vector<uint64_t> HKey;
+
+// Is the multiset {(string_i, value_i)} mapped onto itself by every generator?
+bool multiset_invariant(int group, int n, int W, const std::vector<HKey>& keys,
+                        const std::vector<double>& vals, double rel_tol) {
+  std::map<HKey, std::vector<double>> base;
+  for (size_t i = 0; i < keys.size(); ++i) base[keys[i]].push_back(vals[i]);
+  for (auto& kv : base) std::sort(kv.second.begin(), kv.second.end());
+  for (const auto& g : generators(group, n)) {
+    std::map<HKey, std::vector<double>> img;
+    for (size_t i = 0; i < keys.size(); ++i) {
+      HKey k(2 * W);
+      permute_string(keys[i].data(), keys[i].data() + W, n, W, g, k.data(), k.data() + W);
+      img[k].push_back(vals[i]);
+    }
+    if (img.size() != base.size()) return false;
+    for (auto& kv : img) {
+      auto it = base.find(kv.first);
+      if (it == base.end() || it->second.size() != kv.second.size()) return false;
+      std::sort(kv.second.begin(), kv.second.end());
+      for (size_t t = 0; t < kv.second.size(); ++t) {
+        double a = kv.second[t], b = it->second[t];
+        if (std::fabs(a - b) > rel_tol * std::max(1.0, std::max(std::fabs(a), std::fabs(b))))
+          return false;
+      }
+    }
+  }
+  return true;
+}
+
+bool bloch_invariant(int group, int n, const double* bloch) {
+  for (const auto& g : generators(group, n))
+    for (int q = 0; q < n; ++q)
+      for (int a = 0; a < 3; ++a)
+        if (bloch[3 * q + a] != bloch[3 * g[q] + a]) return false;
+  return true;
+}
+
+pp_status validate_config(const pp_config* cfg) {
+  if (!cfg) return fail(PP_ERR_ARG, "config is null");
+  if (cfg->n_qubits < 1 || cfg->n_qubits > 64 * kMaxW)
+    return fail(PP_ERR_ARG, "n_qubits must be in 1..256");
+  if (cfg->symmetry < PP_SYM_NONE || cfg->symmetry > PP_SYM_SN)
+    return fail(PP_ERR_ARG, "unknown symmetry");
+  if (cfg->batch != 1) return fail(PP_ERR_ARG, "batch must be 1");
+  if (cfg->coef_type != PP_COEF_F64) return fail(PP_ERR_ARG, "only PP_COEF_F64 is supported");
+  if (!(cfg->coeff_eps >= 0.0)) return fail(PP_ERR_ARG, "coeff_eps must be >= 0");
+  if (cfg->noise_mode < PP_NOISE_NONE || cfg->noise_mode > PP_NOISE_PER_LAYER)
+    return fail(PP_ERR_ARG, "unknown noise mode");
+  if (cfg->noise_mode != PP_NOISE_NONE && !(cfg->noise_p >= 0.0))
+    return fail(PP_ERR_ARG, "noise_p must be >= 0");
+  return PP_OK;
+}
+
+pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
+                        const uint64_t* z, const double* coef, bool on_device, pp_ctx** out) {
+  if (!out) return fail(PP_ERR_ARG, "out is null");
+  *out = nullptr;
+  PP_TRY(validate_config(cfg));
+  if (n_terms < 0) return fail(PP_ERR_ARG, "n_terms < 0");
+  if (n_terms > 0 && (!x || !z || !coef)) return fail(PP_ERR_ARG, "null term arrays");
+  if ((uint64_t)n_terms >= (1ull << 31)) return fail(PP_ERR_ARG, "too many input terms");
+  pp_ctx* c = new pp_ctx();
+  c->cfg = *cfg;
+  c->n = cfg->n_qubits;
+  c->W = (c->n + 63) / 64;
+  c->sms = std::max(1, device_sm_count());
+  c->gate_bps = gate_blocks_per_sm(c->W);
+
+  auto cleanup = [&](pp_status st) {
+    pp_destroy(c);
+    return st;
+  };
+  {
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    c->layer_bps = coop ? layer_blocks_per_sm(c->W) : 0;
+    if (cudaEventCreate(&c->ev_layer[0]) != cudaSuccess ||
+        cudaEventCreate(&c->ev_layer[1]) != cudaSuccess)
+      return cleanup(fail(PP_ERR_CUDA, "event creation failed"));
+  }
+  if (cfg->cuda_stream) {
+    c->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    c->own_stream = true;
+  }
+  const int W = c->W;
+  pp_status st;
+  if ((st = dmalloc(c, (void**)&c->d_desc, 3 * sizeof(DevTable))) != PP_OK) return cleanup(st);
+  if ((st = dmalloc(c, (void**)&c->d_ctl, sizeof(DevCtl))) != PP_OK) return cleanup(st);
+  if (cudaMallocHost((void**)&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_out, sizeof(double)) != cudaSuccess)
+    return cleanup(fail(PP_ERR_OOM, "pinned host allocation failed"));
+  memset(c->h_ctl, 0, sizeof(DevCtl));
+  c->overlap_grid = c->sms * 4;
+  if ((st = dmalloc(c, (void**)&c->d_partials, sizeof(double) * c->overlap_grid)) != PP_OK ||
+      (st = dmalloc(c, (void**)&c->d_out, sizeof(double))) != PP_OK ||
+      (st = dmalloc(c, (void**)&c->d_bloch, sizeof(double) * 3 * c->n)) != PP_OK ||
+      (st = dmalloc(c, (void**)&c->d_damp, sizeof(double) * (c->n + 1))) != PP_OK ||
+      (st = dmalloc(c, (void**)&c->d_ldamp, sizeof(double) * (c->n + 1))) != PP_OK)
+    return cleanup(st);
+  {
+    std::vector<double> damp(c->n + 1, 1.0), ldamp(c->n + 1, 1.0);
+    for (int k = 1; k <= c->n; ++k) damp[k] = damp[k - 1] * (1.0 - cfg->noise_p);
+    for (int k = 0; k <= c->n; ++k) ldamp[k] = std::exp(-cfg->noise_p * (double)k);
+    cudaStreamSynchronize(c->stream);
+    if (cudaMemcpy(c->d_damp, damp.data(), damp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_ldamp, ldamp.data(), ldamp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(PP_ERR_CUDA, "constant table upload failed"));
+    DevCtl zero;
+    memset(&zero, 0, sizeof(zero));
+    if (cudaMemcpy(c->d_ctl, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(PP_ERR_CUDA, "control block init failed"));
+  }
+  uint64_t cap = std::max<uint64_t>(4 * (uint64_t)n_terms, 1024);
+  cap = (cap + 1023) & ~1023ull;
+  size_t need = 2 * table_bytes(cap, index_cap_for(cap), W) + c->bytes;
+  if (cfg->mem_budget_bytes && need > cfg->mem_budget_bytes)
+    return cleanup(fail(PP_ERR_CAPACITY, "initial table exceeds the memory budget"));
+  if ((st = alloc_buf(c, c->buf[0], cap)) != PP_OK || (st = alloc_buf(c, c->buf[1], cap)) != PP_OK)
+    return cleanup(st);
+  c->active = 0;
+  if ((st = publish_desc(c)) != PP_OK) return cleanup(st);
+
+  // Observable invariance (host copy needed for the check).
+  std::vector<uint64_t> hx, hz;
+  std::vector<double> hc;
+  if (n_terms > 0) {
+    hx.resize((size_t)n_terms * W);
+    hz.resize((size_t)n_terms * W);
+    hc.resize((size_t)n_terms);
+    if (on_device) {
+      if (cudaMemcpyAsync(hx.data(), x, hx.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaMemcpyAsync(hz.data(), z, hz.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaMemcpyAsync(hc.data(), coef, hc.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cleanup(fail(PP_ERR_CUDA, "reading device term arrays failed"));
+    } else {
+      memcpy(hx.data(), x, hx.size() * 8);
+      memcpy(hz.data(), z, hz.size() * 8);
+      memcpy(hc.data(), coef, hc.size() * 8);
+    }
+    for (int64_t i = 0; i < n_terms; ++i)
+      if (key_has_bits_beyond(&hx[i * W], &hz[i * W], c->n, W))
+        return cleanup(fail(PP_ERR_ARG, "a string has bits at or above n_qubits"));
+  }
+  if (cfg->symmetry != PP_SYM_NONE) {
+    std::map<HKey, double> acc;
+    for (int64_t i = 0; i < n_terms; ++i) {
+      HKey k(2 * W);
+      for (int j = 0; j < W; ++j) {
+        k[j] = hx[i * W + j];
+        k[W + j] = hz[i * W + j];
+      }
+      acc[k] += hc[i];
+    }
+    std::vector<HKey> ks;
+    std::vector<double> vs;
+    for (auto& kv : acc) {
+      ks.push_back(kv.first);
+      vs.push_back(kv.second);
+    }
+    c->obs_invariant = multiset_invariant(cfg->symmetry, c->n, W, ks, vs, 1e-12);
+  }
+
+  // Ingest: pack, then accumulate (with representatives when a group is set).
+  if (n_terms > 0) {
+    uint64_t* d_keys = nullptr;
+    double* d_coef = nullptr;
+    unsigned* d_bad = nullptr;
+    if ((st = dmalloc(c, (void**)&d_keys, (size_t)n_terms * 16 * W)) != PP_OK ||
+        (st = dmalloc(c, (void**)&d_coef, (size_t)n_terms * 8)) != PP_OK)
+      return cleanup(st);
+    std::vector<uint64_t> packed((size_t)n_terms * 2 * W);
+    for (int64_t i = 0; i < n_terms; ++i)
+      for (int j = 0; j < W; ++j) {
+        packed[i * 2 * W + j] = hx[i * W + j];
+        packed[i * 2 * W + W + j] = hz[i * W + j];
+      }
+    (void)d_bad;
+    if (cudaMemcpyAsync(d_keys, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_coef, hc.data(), hc.size() * 8, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+      return cleanup(fail(PP_ERR_CUDA, "term upload failed"));
+    if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return cleanup(st);
+    cudaError_t e = launch_merge_insert(W, cfg->symmetry, c->n, cfg->max_weight,
+                                        grid_for(c, n_terms, 4), c->stream, d_keys, d_coef,
+                                        (uint64_t)n_terms, nullptr, 0, desc_of(c->buf[0]), c->d_ctl);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "merge_insert"));
+    e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c->buf[0]), c->d_ctl,
+                        cfg->coeff_eps);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "finalize"));
+    if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
+    dfree(c, d_keys, (size_t)n_terms * 16 * W);
+    dfree(c, d_coef, (size_t)n_terms * 8);
+  }
+  *out = c;
+  return PP_OK;
+}
+
+// Build the gate arguments of one layer in application (reversed) order.
+pp_status build_gates(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
+                      std::vector<GateArgs>& out) {
+  const int W = c->W;
+  out.clear();
+  for (int t = n_gates - 1; t >= 0; --t) {
+    const pp_pauli& P = gates[t];
+    for (int j = W; j < kMaxW; ++j)
+      if (P.x[j] || P.z[j]) return fail(PP_ERR_ARG, "gate has bits in unused words");
+    if (key_has_bits_beyond(P.x, P.z, c->n, W))
+      return fail(PP_ERR_ARG, "gate has bits at or above n_qubits");
+    if (!std::isfinite(theta[t])) return fail(PP_ERR_ARG, "non-finite angle");
+    GateArgs g;
+    memset(&g, 0, sizeof(g));
+    int pyy = 0, pivot = -1;
+    uint64_t pmask = 0;
+    for (int j = 0; j < W; ++j) {
+      g.px[j] = P.x[j];
+      g.pz[j] = P.z[j];
+      g.supp[j] = P.x[j] | P.z[j];
+      pyy += popcount64(P.x[j] & P.z[j]);
+    }
+    for (int j = 0; j < 2 * W && pivot < 0; ++j) {
+      uint64_t w = j < W ? P.x[j] : P.z[j - W];
+      if (w) {
+        pivot = j;
+        pmask = w & (~w + 1);
+      }
+    }
+    if (pivot < 0) continue;  // identity generator: a global phase, nothing to do
+    g.cth = std::cos(theta[t]);
+    g.sth = std::sin(theta[t]);
+    g.damp = (c->cfg.noise_mode == PP_NOISE_PER_GATE) ? c->d_damp : nullptr;
+    g.eps = c->cfg.coeff_eps;
+    g.use_eps = c->cfg.coeff_eps > 0.0 ? 1 : 0;
+    memcpy(&g.eps_bits, &g.eps, 8);
+    g.wmax = c->cfg.max_weight;
+    g.pyy = pyy & 3;
+    if (pivot < W)
+      g.pvx[pivot] = pmask;
+    else
+      g.pvz[pivot - W] = pmask;
+    g.gate_id = (unsigned)out.size();
+    out.push_back(g);
+  }
+  return PP_OK;
+}
+
+pp_status ensure_events(pp_ctx* c, size_t k) {
+  while (c->ev_start.size() < k) {
+    cudaEvent_t a, b;
+    PP_CUDA(cudaEventCreate(&a));
+    PP_CUDA(cudaEventCreate(&b));
+    c->ev_start.push_back(a);
+    c->ev_end.push_back(b);
+  }
+  return PP_OK;
+}
+
+// Queue the gate kernels; with profile_kernels each is bracketed by event
+// records (inside a capture they must be external records to become event
+// nodes of the graph).
+cudaError_t enqueue_gates(pp_ctx* c, const std::vector<GateArgs>& args, int grid, bool capturing) {
+  const DevTable* tab = c->d_desc + 2;
+  const bool prof = c->cfg.profile_kernels != 0;
+  const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  for (size_t k = 0; k < args.size(); ++k) {
+    cudaError_t e;
+    if (prof && (e = cudaEventRecordWithFlags(c->ev_start[k], c->stream, flags)) != cudaSuccess)
+      return e;
+    if ((e = launch_gate(c->W, grid, c->stream, tab, c->d_ctl, args[k], k > 0)) != cudaSuccess)
+      return e;
+    if (prof && (e = cudaEventRecordWithFlags(c->ev_end[k], c->stream, flags)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+pp_status launch_layer_gates(pp_ctx* c, const std::vector<GateArgs>& args, int grid) {
+  if (c->cfg.profile_kernels) PP_TRY(ensure_events(c, args.size()));
+  c->launches += (int64_t)args.size();
+  if (!c->cfg.use_graphs || args.size() < 2) {
+    PP_CUDA(enqueue_gates(c, args, grid, false));
+    return PP_OK;
+  }
+  std::vector<unsigned char> sig(args.size() * sizeof(GateArgs));
+  memcpy(sig.data(), args.data(), sig.size());
+  c->graph_clock++;
+  for (auto& e : c->graphs) {
+    if (e.grid == grid && e.sig == sig) {
+      e.last_use = c->graph_clock;
+      PP_CUDA(cudaGraphLaunch(e.exec, c->stream));
+      return PP_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  PP_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = enqueue_gates(c, args, grid, true);
+  if (ce != cudaSuccess) {
+    cudaStreamEndCapture(c->stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ce, "gate launch during capture");
+  }
+  PP_CUDA(cudaStreamEndCapture(c->stream, &graph));
+  GraphEntry ent;
+  ent.sig = std::move(sig);
+  ent.grid = grid;
+  ent.last_use = c->graph_clock;
+  cudaError_t e = cudaGraphInstantiate(&ent.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  if (c->graphs.size() >= 16) {
+    auto it = std::min_element(c->graphs.begin(), c->graphs.end(),
+                               [](const GraphEntry& a, const GraphEntry& b) {
+                                 return a.last_use < b.last_use;
+                               });
+    cudaGraphExecDestroy(it->exec);
+    c->graphs.erase(it);
+  }
+  c->graphs.push_back(std::move(ent));
+  PP_CUDA(cudaGraphLaunch(c->graphs.back().exec, c->stream));
+  return PP_OK;
+}
+
+// Add the durations of gate kernels [from, to) of the last launch (the
+// stream has been synchronised).
+pp_status collect_gate_times(pp_ctx* c, unsigned from, unsigned to) {
+  if (!c->cfg.profile_kernels) return PP_OK;
+  for (unsigned k = from; k < to && k < c->ev_start.size(); ++k) {
+    float ms = 0.f;
+    PP_CUDA(cudaEventElapsedTime(&ms, c->ev_start[k], c->ev_end[k]));
+    c->gate_ms += ms;
+    c->gates_timed++;
+  }
+  return PP_OK;
+}
+
+// Device copy of a layer's gate arguments (cached by content).
+pp_status device_args(pp_ctx* c, const std::vector<GateArgs>& args, const GateArgs** out) {
+  std::vector<unsigned char> sig(args.size() * sizeof(GateArgs));
+  memcpy(sig.data(), args.data(), sig.size());
+  c->graph_clock++;
+  for (auto& e : c->arg_cache) {
+    if (e.sig == sig) {
+      e.last_use = c->graph_clock;
+      *out = e.d_args;
+      return PP_OK;
+    }
+  }
+  if (c->arg_cache.size() >= 16) {
+    auto it = std::min_element(c->arg_cache.begin(), c->arg_cache.end(),
+                               [](const ArgsEntry& a, const ArgsEntry& b) {
+                                 return a.last_use < b.last_use;
+                               });
+    dfree(c, it->d_args, it->n * sizeof(GateArgs));
+    c->arg_cache.erase(it);
+  }
+  ArgsEntry ent;
+  ent.n = args.size();
+  PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n * sizeof(GateArgs)));
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  PP_CUDA(cudaMemcpy(ent.d_args, args.data(), ent.n * sizeof(GateArgs), cudaMemcpyHostToDevice));
+  ent.sig = std::move(sig);
+  ent.last_use = c->graph_clock;
+  *out = ent.d_args;
+  c->arg_cache.push_back(std::move(ent));
+  return PP_OK;
+}
+
+pp_status ensure_merged(pp_ctx* c) {
+  if (c->merged) return PP_OK;
+  return merge_active(c, PP_SYM_NONE);
+}
+
+}  // namespace
+
+extern "C" {
+
+pp_status pp_config_default(pp_config* cfg) {
+  if (!cfg) return fail(PP_ERR_ARG, "config is null");
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->symmetry = PP_SYM_NONE;
+  cfg->batch = 1;
+  cfg->coef_type = PP_COEF_F64;
+  cfg->coeff_eps = 0.0;
+  cfg->max_weight = -1;
+  cfg->noise_mode = PP_NOISE_NONE;
+  cfg->noise_p = 0.0;
+  cfg->mem_budget_bytes = 0;
+  cfg->cuda_stream = nullptr;
+  cfg->check_symmetry = 1;
+  cfg->use_graphs = 1;
+  cfg->profile_kernels = 0;
+  cfg->layer_kernel = 1;
+  return PP_OK;
+}
+
+pp_status pp_create(const pp_config* cfg, int64_t n_terms, const uint64_t* x, const uint64_t* z,
+                    const double* coef, pp_ctx** out) {
+  return create_common(cfg, n_terms, x, z, coef, false, out);
+}
+
+pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
+                           const uint64_t* z, const double* coef, pp_ctx** out) {
+  return create_common(cfg, n_terms, x, z, coef, true, out);
+}
+
+pp_status pp_destroy(pp_ctx* c) {
+  if (!c) return PP_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+  c->graphs.clear();
+  for (auto e : c->ev_start) cudaEventDestroy(e);
+  for (auto e : c->ev_end) cudaEventDestroy(e);
+  for (auto& a : c->arg_cache) dfree(c, a.d_args, a.n * sizeof(GateArgs));
+  c->arg_cache.clear();
+  for (auto e : c->ev_layer)
+    if (e) cudaEventDestroy(e);
+  free_buf(c, c->buf[0]);
+  free_buf(c, c->buf[1]);
+  dfree(c, c->d_desc, 3 * sizeof(DevTable));
+  dfree(c, c->d_ctl, sizeof(DevCtl));
+  dfree(c, c->d_damp, sizeof(double) * (c->n + 1));
+  dfree(c, c->d_ldamp, sizeof(double) * (c->n + 1));
+  dfree(c, c->d_partials, sizeof(double) * c->overlap_grid);
+  dfree(c, c->d_out, sizeof(double));
+  dfree(c, c->d_bloch, sizeof(double) * 3 * c->n);
+  size_t sn = (size_t)(c->n + 1) * (c->n + 1) * (c->n + 1) * sizeof(double);
+  dfree(c, c->d_sn, sn);
+  dfree(c, c->d_sn_work, sn);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PP_OK;
+}
+
+pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
+                         int symmetric_boundary) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (n_gates < 0 || (n_gates > 0 && (!gates || !theta)))
+    return fail(PP_ERR_ARG, "bad gate arrays");
+  std::vector<GateArgs> args;
+  PP_TRY(build_gates(c, n_gates, gates, theta, args));
+  if (c->cfg.symmetry != PP_SYM_NONE && c->cfg.check_symmetry && n_gates > 0) {
+    std::vector<HKey> ks;
+    std::vector<double> vs;
+    for (int t = 0; t < n_gates; ++t) {
+      HKey k(2 * c->W);
+      for (int j = 0; j < c->W; ++j) {
+        k[j] = gates[t].x[j];
+        k[c->W + j] = gates[t].z[j];
+      }
+      ks.push_back(k);
+      vs.push_back(theta[t]);
+    }
+    if (!multiset_invariant(c->cfg.symmetry, c->n, c->W, ks, vs, 0.0))
+      return fail(PP_ERR_SYMMETRY, "layer gate multiset is not invariant under the group");
+  }
+  PP_TRY(ensure_merged(c));
+  if (c->cfg.noise_mode == PP_NOISE_PER_LAYER && c->n_terms > 0) {
+    PP_CUDA(launch_damp_layer(c->W, grid_for(c, c->n_terms, 4), c->stream,
+                              desc_of(c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
+    c->launches += 1;
+  }
+  PP_TRY(make_room(c));
+  const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
+  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0;
+  int grid_b = 1;
+  if (layered) {
+    // persistent: one string per thread per pass, never more blocks than can
+    // be co-resident (the grid barrier needs all of them)
+    const uint64_t want = (est + kBlock - 1) / kBlock;
+    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
+  } else {
+    // a power of two so that captured graphs are reused
+    while ((uint64_t)grid_b * kBlock < est) grid_b <<= 1;
+    grid_b = std::min(grid_b, c->sms * c->gate_bps);
+  }
+  const GateArgs* d_args = nullptr;
+  if (layered && !args.empty()) PP_TRY(device_args(c, args, &d_args));
+  if (!args.empty()) {
+    unsigned first = 0;
+    for (;;) {
+      PP_CUDA(launch_chain_init(c->stream, c->d_ctl, first));
+      if (layered) {
+        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[0], c->stream));
+        PP_CUDA(launch_layer(c->W, grid_b, c->stream, c->d_desc + 2, c->d_ctl, d_args,
+                             (unsigned)args.size()));
+        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[1], c->stream));
+        c->launches += 1;
+      } else {
+        PP_TRY(launch_layer_gates(c, args, grid_b));
+      }
+      PP_CUDA(launch_chain_finish(c->stream, c->d_ctl, (unsigned)args.size()));
+      c->launches += 2;
+      PP_TRY(read_ctl(c));
+      PP_TRY(check_device_error(c));
+      const unsigned end = c->h_ctl->stall ? c->h_ctl->stall - 1u : (unsigned)args.size();
+      if (layered) {
+        if (c->cfg.profile_kernels && end > first) {
+          float ms = 0.f;
+          PP_CUDA(cudaEventElapsedTime(&ms, c->ev_layer[0], c->ev_layer[1]));
+          c->gate_ms += ms;
+          c->gates_timed++;
+        }
+      } else {
+        PP_TRY(collect_gate_times(c, first, end));
+      }
+      c->n_terms = c->h_ctl->n_terms;
+      c->n_live = c->h_ctl->n_live;
+      if (!c->h_ctl->stall) break;
+      // gate `end` found too little room: compact and grow, then resume there
+      PP_TRY(make_room(c));
+      first = end;
+    }
+  }
+  if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE) {
+    PP_TRY(merge_active(c, c->cfg.symmetry));
+  }
+  return PP_OK;
+}
+
+pp_status pp_canonicalize(pp_ctx* c) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (c->cfg.symmetry == PP_SYM_NONE) return fail(PP_ERR_STATE, "context has no symmetry");
+  if (c->n_terms == 0) return PP_OK;
+  Buf& b = c->buf[c->active];
+  PP_CUDA(launch_canon_inplace(c->W, c->cfg.symmetry, c->n, grid_for(c, c->n_terms, 4), c->stream,
+                               b.keys, b.keys, c->n_terms));
+  c->launches += 1;
+  c->merged = false;
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  return PP_OK;
+}
+
+pp_status pp_merge(pp_ctx* c) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  return merge_active(c, PP_SYM_NONE);
+}
+
+pp_status pp_truncate(pp_ctx* c, double eps, int max_weight) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (!(eps >= 0.0)) return fail(PP_ERR_ARG, "eps must be >= 0");
+  PP_TRY(ensure_merged(c));
+  return compact_into(c, 1 - c->active, eps, max_weight);
+}
+
+pp_status pp_expect(pp_ctx* c, const double* bloch, double* out) {
+  if (!c || !bloch || !out) return fail(PP_ERR_ARG, "null argument");
+  const int n = c->n, W = c->W;
+  for (int i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(bloch[i])) return fail(PP_ERR_ARG, "non-finite Bloch component");
+  OverlapArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.group = c->cfg.symmetry;
+  if (a.group != PP_SYM_NONE) {
+    if (bloch_invariant(a.group, n, bloch)) {
+      a.group = PP_SYM_NONE;  // Eq. 2: orbit members have equal overlaps
+    } else if (!c->obs_invariant) {
+      return fail(PP_ERR_SYMMETRY, "neither the state nor the observable is invariant");
+    }
+  }
+  bool basis = true;
+  for (int q = 0; q < n && basis; ++q)
+    basis = bloch[3 * q] == 0.0 && bloch[3 * q + 1] == 0.0 &&
+            (bloch[3 * q + 2] == 1.0 || bloch[3 * q + 2] == -1.0);
+  if (basis) {
+    a.basis = 1;
+    for (int q = 0; q < n; ++q)
+      if (bloch[3 * q + 2] == -1.0) a.bits[q >> 6] |= 1ull << (q & 63);
+  }
+  PP_CUDA(cudaMemcpyAsync(c->d_bloch, bloch, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                          c->stream));
+  a.bloch = c->d_bloch;
+  if (a.group == PP_SYM_SN) {
+    size_t sn = (size_t)(n + 1) * (n + 1) * (n + 1);
+    if (!c->d_sn) {
+      PP_TRY(dmalloc(c, (void**)&c->d_sn, sn * sizeof(double)));
+      PP_TRY(dmalloc(c, (void**)&c->d_sn_work, sn * sizeof(double)));
+    }
+    std::vector<double> bv(bloch, bloch + 3 * n);
+    if (bv != c->sn_bloch) {
+      PP_CUDA(launch_sn_table(n, c->stream, c->d_bloch, c->d_sn_work, c->d_sn));
+      c->launches += 1;
+      c->sn_bloch = bv;
+    }
+    a.sn_table = c->d_sn;
+  }
+  PP_CUDA(launch_overlap(W, c->overlap_grid, c->stream, c->buf[c->active].keys,
+                         c->buf[c->active].coef, c->n_terms, nullptr, a, c->d_partials, c->d_out));
+  c->launches += 2;
+  PP_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  *out = *c->h_out;
+  return PP_OK;
+}
+
+pp_status pp_num_terms(pp_ctx* c, int64_t* live, int64_t* stored) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  PP_TRY(read_ctl(c));
+  c->n_terms = c->h_ctl->n_terms;
+  c->n_live = c->h_ctl->n_live;
+  if (live) *live = c->n_live;
+  if (stored) *stored = (int64_t)c->n_terms;
+  return PP_OK;
+}
+
+pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, double* coef,
+                    int64_t* n_out) {
+  if (!c || !n_out) return fail(PP_ERR_ARG, "null argument");
+  PP_TRY(ensure_merged(c));
+  PP_TRY(read_ctl(c));
+  const int W = c->W;
+  int spare = 1 - c->active;
+  Buf& d = c->buf[spare];
+  // compact into the spare table without an index, then copy it out
+  PP_TRY(ctl_prepare_insert(c, 0));
+  PP_CUDA(launch_compact(W, grid_for(c, c->n_terms, 4), c->stream, desc_of(c->buf[c->active]),
+                         c->n_terms, desc_of(d), 0, c->cfg.coeff_eps, 0.0, -1, c->d_ctl));
+  c->launches += 1;
+  PP_TRY(read_ctl(c));
+  PP_TRY(check_device_error(c));
+  const int64_t m = (int64_t)c->h_ctl->n_next;
+  // restore the control block of the live table
+  PP_TRY(ctl_prepare_insert(c, c->n_terms));
+  {
+    long long live = c->n_live;
+    PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_live, &live, 8, cudaMemcpyHostToDevice, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  *n_out = m;
+  if (capacity < m) return fail(PP_ERR_ARG, "export capacity too small");
+  if (m == 0) return PP_OK;
+  if (!x || !z || !coef) return fail(PP_ERR_ARG, "null output arrays");
+  std::vector<uint64_t> packed((size_t)m * 2 * W);
+  PP_CUDA(cudaMemcpyAsync(packed.data(), d.keys, packed.size() * 8, cudaMemcpyDeviceToHost,
+                          c->stream));
+  PP_CUDA(cudaMemcpyAsync(coef, d.coef, (size_t)m * 8, cudaMemcpyDeviceToHost, c->stream));
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < m; ++i)
+    for (int j = 0; j < W; ++j) {
+      x[i * W + j] = packed[i * 2 * W + j];
+      z[i * W + j] = packed[i * 2 * W + W + j];
+    }
+  return PP_OK;
+}
+
+pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
+  if (!c || !out) return fail(PP_ERR_ARG, "null argument");
+  PP_TRY(read_ctl(c));
+  out->live_terms = c->h_ctl->n_live;
+  out->stored_terms = (int64_t)c->h_ctl->n_terms;
+  out->capacity = (int64_t)c->buf[c->active].cap;
+  out->gate_updates = c->h_ctl->updates;
+  out->gates_applied = (int64_t)c->h_ctl->gates_done;
+  out->merges = c->merges;
+  out->compactions = c->compactions;
+  out->regrows = c->regrows;
+  out->device_bytes = c->bytes;
+  out->anticommuting_terms = (double)c->h_ctl->ac_total;
+  out->kernel_launches = c->launches;
+  out->gate_kernel_ms = c->gate_ms;
+  out->gate_kernels_timed = c->gates_timed;
+  return PP_OK;
+}
+
+pp_status pp_set_budget(pp_ctx* c, size_t mem_budget_bytes) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  c->cfg.mem_budget_bytes = mem_budget_bytes;
+  return PP_OK;
+}
+
+pp_status pp_synchronize(pp_ctx* c) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  return PP_OK;
+}
+
+const char* pp_last_error(void) { return g_last_error.c_str(); }
+
+// ----------------------------------------------------------- stateless calls
+
+pp_status pp_canonical_keys(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                            uint64_t* keys_out, void* stream) {
+  if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
+  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (m < 0 || (m > 0 && (!keys_in || !keys_out))) return fail(PP_ERR_ARG, "bad arrays");
+  if (m == 0) return PP_OK;
+  const int W = (n_qubits + 63) / 64;
+  int sms = std::max(1, device_sm_count());
+  int grid = (int)std::min<int64_t>((m + kBlock * 4 - 1) / (kBlock * 4), (int64_t)sms * 8);
+  PP_CUDA(launch_canon_inplace(W, symmetry, n_qubits, std::max(grid, 1), (cudaStream_t)stream,
+                               keys_out, keys_in, (uint64_t)m));
+  return PP_OK;
+}
+
+pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                         const double* coef_in, uint64_t* keys_out, double* coef_out,
+                         int64_t* m_out, void* stream) {
+  if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
+  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (!m_out || m < 0 || (m > 0 && (!keys_in || !coef_in || !keys_out || !coef_out)))
+    return fail(PP_ERR_ARG, "bad arrays");
+  if ((uint64_t)m >= (1ull << 31)) return fail(PP_ERR_ARG, "too many terms");
+  *m_out = 0;
+  if (m == 0) return PP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int W = (n_qubits + 63) / 64;
+  const uint64_t icap = next_pow2(2 * (uint64_t)m);
+  uint64_t* index = nullptr;
+  DevCtl* ctl = nullptr;
+  PP_CUDA(cudaMallocAsync((void**)&index, icap * 8, s));
+  cudaError_t e = cudaMallocAsync((void**)&ctl, sizeof(DevCtl), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(index, s);
+    return cuda_fail(e, "cudaMallocAsync");
+  }
+  DevTable dst;
+  dst.keys = keys_out;
+  dst.coef = coef_out;
+  dst.index = index;
+  dst.cap = (uint64_t)m;
+  dst.imask = icap - 1;
+  int sms = std::max(1, device_sm_count());
+  int grid = (int)std::min<int64_t>((m + kBlock * 4 - 1) / (kBlock * 4), (int64_t)sms * 8);
+  DevCtl h;
+  memset(&h, 0, sizeof(h));
+  if ((e = cudaMemsetAsync(index, 0, icap * 8, s)) == cudaSuccess &&
+      (e = cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s)) == cudaSuccess &&
+      (e = launch_merge_insert(W, symmetry, n_qubits, -1, std::max(grid, 1), s, keys_in, coef_in,
+                               (uint64_t)m, nullptr, 0, dst, ctl)) == cudaSuccess &&
+      (e = cudaMemcpyAsync(&h, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s)) == cudaSuccess) {
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFreeAsync(index, s);
+  cudaFreeAsync(ctl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pp_merge_terms");
+  if (h.error) return fail(PP_ERR_INTERNAL, "device error in merge");
+  *m_out = (int64_t)h.n_next;
+  return PP_OK;
+}
+
+pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* keys,
+                         const double* coef, const double* bloch, double* out, void* stream) {
+  if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
+  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (m < 0 || !out || !bloch || (m > 0 && (!keys || !coef))) return fail(PP_ERR_ARG, "bad arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int W = (n_qubits + 63) / 64;
+  int sms = std::max(1, device_sm_count());
+  int grid = sms * 4;
+  double* partials = nullptr;
+  double *sn = nullptr, *work = nullptr;
+  size_t snb = (size_t)(n_qubits + 1) * (n_qubits + 1) * (n_qubits + 1) * sizeof(double);
+  PP_CUDA(cudaMallocAsync((void**)&partials, sizeof(double) * grid, s));
+  cudaError_t e = cudaSuccess;
+  if (symmetry == PP_SYM_SN) {
+    if ((e = cudaMallocAsync((void**)&sn, snb, s)) == cudaSuccess)
+      e = cudaMallocAsync((void**)&work, snb, s);
+  }
+  OverlapArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n_qubits;
+  a.group = symmetry;
+  a.basis = 0;
+  a.bloch = bloch;
+  a.sn_table = sn;
+  if (e == cudaSuccess && symmetry == PP_SYM_SN) e = launch_sn_table(n_qubits, s, bloch, work, sn);
+  if (e == cudaSuccess)
+    e = launch_overlap(W, grid, s, keys, coef, (uint64_t)m, nullptr, a, partials, out);
+  if (partials) cudaFreeAsync(partials, s);
+  if (sn) cudaFreeAsync(sn, s);
+  if (work) cudaFreeAsync(work, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pp_overlap_sum");
+  return PP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Internal declarations shared by the kernels (pp_kernels.cu) and the host
+// side of the C ABI (pp_api.cu).  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace ppk {
+
+constexpr int kMaxW = 4;                    // up to 256 qubits
+constexpr uint32_t kPendingIdx = 0xFFFFFFFFu;  // index slot claimed, dense position not yet published
+constexpr int kBlock = 256;
+
+// Device-side error bits (DevCtl::error / err_pending).
+enum : unsigned {
+  kErrProbe = 1u,    // a hash probe walked the whole index without finding a slot
+  kErrTimeout = 2u,  // a bounded wait for a published slot ran out
+  kErrAppend = 4u,   // an append went past the dense capacity
+};
+
+// Term table: dense arrays of keys and coefficients plus an open-addressing
+// index from key to dense position.
+//   keys  [cap][2W]  x words then z words of each string
+//   coef  [cap]      FP64 coefficient; a truncated entry holds +0.0
+//   index [icap]     slot = (tag << 32) | dense position, 0 = empty
+struct DevTable {
+  uint64_t* keys;
+  double* coef;
+  uint64_t* index;
+  uint64_t cap;
+  uint64_t imask;  // icap - 1, icap a power of two >= 2 cap
+};
+
+// Per-context counters in device memory.
+//
+// Between operations the table size is (n_terms, n_live).  Inside a layer the
+// gate kernels pass it along without any end-of-kernel bookkeeping: gate g
+// (layer-local id) reads its input size from slot (g+2)%3, records it in slot
+// g%3, appends births by atomics on cnt[g%3], accumulates its live-count
+// change in dlt[g%3], and clears slot (g+1)%3 for gate g+1.  Every block of a
+// gate therefore reads the same, final values written by gate g-1.  Lines hit
+// by many blocks are kept apart so that different L2 slices serve them.
+struct alignas(128) DevCtl {
+  unsigned long long n_terms;  // stored entries [0, n_terms) between operations
+  long long n_live;            // entries holding a kept coefficient
+  unsigned int stall;          // 1 + id of a gate that found too little capacity; 0 = none
+  unsigned int first_gate;     // gates with a smaller layer-local id skip themselves
+  unsigned int error;          // error bits (any kernel)
+  unsigned int pad0;
+  alignas(128) unsigned long long base[3];  // stored entries entering the gate of a slot
+  long long live_base[3];                   // live entries entering the gate of a slot
+  alignas(128) unsigned long long cnt[3];   // births appended by the gate of a slot
+  alignas(128) long long dlt[3];            // live-count change by the gate of a slot
+  alignas(128) double updates;              // sum of live terms entering each gate
+  unsigned long long gates_done;
+  unsigned long long ac_total;              // sum of live anticommuting terms per gate
+  alignas(128) unsigned long long n_next;   // append cursor of merge / compaction kernels
+  alignas(128) unsigned int bar_root;       // grid-barrier counter of the cooperative layer
+                                            // kernel (grows by gridDim per barrier)
+};
+
+struct GateArgs {
+  uint64_t px[kMaxW], pz[kMaxW], supp[kMaxW];
+  double cth, sth;         // cos(theta), sin(theta), computed on the host
+  const double* damp;      // (1-p)^k, k = 0..n, or nullptr when no per-gate noise
+  double eps;              // coefficient truncation; 0 = off
+  uint64_t eps_bits;       // bit pattern of eps: |c| < eps  <=>  (bits(c) & ~sign) < eps_bits
+  int use_eps;             // eps > 0
+  int wmax;                // weight truncation; < 0 = off
+  int pyy;                 // popcount(px & pz) mod 4 (the Y count of P)
+  uint64_t pvx[kMaxW], pvz[kMaxW];  // one bit of P (x or z plane): the pair member
+                                    // with this bit clear owns the pair
+  unsigned int gate_id;    // layer-local position in application order
+};
+
+struct OverlapArgs {
+  int n;
+  int group;        // 0 plain, 1 Z_n orbit average, 2 S_n table lookup
+  int basis;        // 1: rho is a computational basis state given by bits
+  uint64_t bits[kMaxW];
+  const double* bloch;     // [n][3] device array (product mode)
+  const double* sn_table;  // [(n+1)^3] orbit-averaged overlaps (group 2)
+};
+
+// ---------------------------------------------------------------- launchers
+// All return the launch status; W is the number of words per mask.
+
+// Before the first gate of a (resumed) layer: slot (first+2)%3 <- (n_terms,
+// n_live), counters of slot first%3 cleared, stall cleared.
+cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate);
+// After the gates of a layer (n_gates of them): (n_terms, n_live) <- the state
+// after the last gate that ran.
+cudaError_t launch_chain_finish(cudaStream_t s, DevCtl* ctl, unsigned n_gates);
+
+// All gates of a layer in one cooperative launch (grid <= co-resident blocks);
+// gates points to n_gates GateArgs in device memory.
+cudaError_t launch_layer(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                         const GateArgs* gates, unsigned n_gates);
+int layer_blocks_per_sm(int W);  // co-resident layer-kernel blocks per SM (0: unknown)
+
+// One gate kernel.  With pdl set it is launched with programmatic stream
+// serialisation: it may start while the previous kernel on the stream
+// finishes and waits (griddepcontrol) before touching any data.
+cudaError_t launch_gate(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                        const GateArgs& g, bool pdl);
+
+// src entries [0, count) (count read from *count_dev when count_dev != null)
+// -> drop those heavier than wmax (>= 0) -> representatives under `group`
+// -> accumulate into dst (dst index clear, ctl->n_next = first free dense
+// position).  Entries whose coefficient is +0.0 are skipped when skip_zero.
+cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cudaStream_t s,
+                                const uint64_t* src_keys, const double* src_coef,
+                                uint64_t count, const unsigned long long* count_dev,
+                                int skip_zero, DevTable dst, DevCtl* ctl);
+
+// Coefficient truncation (eps > 0) of dst entries [0, ctl->n_next); adds the
+// live count to ctl->n_live.
+cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps);
+
+// Copy entries of src[0, count) that are kept (not truncated under eps, and
+// |c| >= extra_eps when extra_eps > 0, weight <= extra_wmax when >= 0) into
+// dst, ctl->n_next as append cursor; inserts into dst's (clear) index when
+// with_index.  Adds the copied count to ctl->n_live.
+cudaError_t launch_compact(int W, int grid, cudaStream_t s, DevTable src, uint64_t count,
+                           DevTable dst, int with_index, double eps, double extra_eps,
+                           int extra_wmax, DevCtl* ctl);
+
+// keys[i] = representative of keys_in[i] (keys may equal keys_in).
+cudaError_t launch_canon_inplace(int W, int group, int n, int grid, cudaStream_t s,
+                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count);
+
+// c <- c * table[weight(Q)] then coefficient truncation, over [0, n_terms);
+// adds the change of the live count to ctl->n_live.
+cudaError_t launch_damp_layer(int W, int grid, cudaStream_t s, DevTable t, DevCtl* ctl,
+                              const double* table, double eps);
+
+// sum_i coef[i] ov(keys[i]) -> partials[grid] -> out[0] (two passes, fixed order).
+cudaError_t launch_overlap(int W, int grid, cudaStream_t s, const uint64_t* keys,
+                           const double* coef, uint64_t count,
+                           const unsigned long long* count_dev, const OverlapArgs& a,
+                           double* partials, double* out);
+
+// S_n orbit-averaged overlap table [(n+1)^3] for a product state (one block);
+// work is a scratch buffer of the same size.
+cudaError_t launch_sn_table(int n, cudaStream_t s, const double* bloch, double* work,
+                            double* table);
+
+// x [m][W], z [m][W] (device) -> keys [m][2W]; *bad |= 1 if a string has
+// bits at or above n.
+cudaError_t launch_pack_keys(int W, int n, int grid, cudaStream_t s, const uint64_t* x,
+                             const uint64_t* z, uint64_t m, uint64_t* keys, unsigned* bad);
+
+int device_sm_count();
+int gate_blocks_per_sm(int W);  // resident gate-kernel blocks per SM
+
+}  // namespace ppk

@@ -1,0 +1,1280 @@
+// CUDA kernels of the Pauli propagation hot path (sm_103a).
+//
+// Data layout (one term table):
+//   keys  [cap][2W] uint64   x words then z words; loaded as W 16-byte vectors
+//   coef  [cap]     double   +0.0 marks a truncated entry when eps > 0
+//   index [icap]    uint64   (tag << 32) | dense position; 0 = empty slot
+//
+// Per gate (Appendix A, Prop. 1 proof, with U = exp(-i theta P / 2)):
+//   Q commutes with P      -> Q unchanged (only per-gate damping)
+//   Q anticommutes with P  -> cos(theta) Q + sin(theta) (i P Q),  i P Q = sigma R,
+//                             R = Q xor P.
+// Q and R = Q xor P form a pair that the gate mixes by a 2x2 rotation.  One
+// thread owns each pair (the member whose "pivot" bit of P is clear), reads
+// both coefficients and writes both results, so the update needs no atomics
+// and is computed exactly as cos*c_Q + (+-sin*c_R) in FP64 without FMA
+// contraction.  A partner that is not in the table is appended (warp ballot
+// + one atomic per warp) and inserted into the index; it is unique to its
+// parent, so the insert never races with another insert of the same key.
+#include <cooperative_groups.h>
+
+#include "pp_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ppk {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSpinLimit = 1 << 22;
+
+template <int W>
+struct Key {
+  uint64_t w[2 * W];  // x[0..W), z[0..W)
+  __device__ __forceinline__ uint64_t& x(int i) { return w[i]; }
+  __device__ __forceinline__ uint64_t& z(int i) { return w[W + i]; }
+  __device__ __forceinline__ uint64_t x(int i) const { return w[i]; }
+  __device__ __forceinline__ uint64_t z(int i) const { return w[W + i]; }
+};
+
+template <int W>
+__device__ __forceinline__ Key<W> ld_key(const uint64_t* __restrict__ keys, uint64_t i) {
+  Key<W> k;
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ulonglong2 v = __ldg(p + j);
+    k.w[2 * j] = v.x;
+    k.w[2 * j + 1] = v.y;
+  }
+  return k;
+}
+
+// Load through L2 only (entries that other threads may have written in the
+// same kernel).
+template <int W>
+__device__ __forceinline__ Key<W> ld_key_cg(const uint64_t* keys, uint64_t i) {
+  Key<W> k;
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ulonglong2 v = __ldcg(p + j);
+    k.w[2 * j] = v.x;
+    k.w[2 * j + 1] = v.y;
+  }
+  return k;
+}
+
+template <int W>
+__device__ __forceinline__ void st_key(uint64_t* keys, uint64_t i, const Key<W>& k) {
+  ulonglong2* p = reinterpret_cast<ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) p[j] = make_ulonglong2(k.w[2 * j], k.w[2 * j + 1]);
+}
+
+template <int W>
+__device__ __forceinline__ bool keys_equal(const Key<W>& a, const Key<W>& b) {
+  bool eq = true;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) eq &= (a.w[j] == b.w[j]);
+  return eq;
+}
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t key_hash(const Key<W>& k) {
+  uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) h = fmix64(h ^ k.w[j]);
+  return h;
+}
+
+__device__ __forceinline__ uint32_t tag_of(uint64_t h) { return (uint32_t)(h >> 32) | 0x80000000u; }
+
+template <int W>
+__device__ __forceinline__ int weight(const Key<W>& k) {
+  int w = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) w += __popcll(k.x(j) | k.z(j));
+  return w;
+}
+
+// Find key k in the index.  Returns its dense position, -1 when it is not
+// present, or -2 (error bit set) when the probe bound is exhausted.
+template <int W>
+__device__ __forceinline__ int64_t index_find(const DevTable& t, const Key<W>& k, uint64_t h,
+                                              uint32_t tag, unsigned& err) {
+  uint64_t pos = h & t.imask;
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
+    if (s == 0) return -1;
+    if ((uint32_t)(s >> 32) == tag) {
+      uint32_t idx = (uint32_t)s;
+      if (idx != kPendingIdx && keys_equal(ld_key_cg<W>(t.keys, idx), k)) return (int64_t)idx;
+    }
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+  return -2;
+}
+
+// Claim an empty slot for a key whose dense position is already written.
+__device__ __forceinline__ void index_claim(const DevTable& t, uint64_t pos, uint64_t val,
+                                            unsigned& err) {
+  unsigned long long* idx = reinterpret_cast<unsigned long long*>(t.index);
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    if (atomicCAS(idx + pos, 0ull, (unsigned long long)val) == 0ull) return;
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------- gate kernel
+
+template <int W>
+__device__ __forceinline__ int sigma_of(const GateArgs& g, const Key<W>& q) {
+  // P Q = i^E R with E = sum_sites px pz + qx qz + 2 pz qx - (px^qx)(pz^qz)
+  // (P = i^{px pz} X^px Z^pz per site); i P Q = i^{E+1} R and E+1 is even.
+  int e = g.pyy;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    e += __popcll(q.x(j) & q.z(j)) + 2 * __popcll(g.pz[j] & q.x(j)) -
+         __popcll((g.px[j] ^ q.x(j)) & (g.pz[j] ^ q.z(j)));
+  }
+  return ((e + 1) & 3) == 0 ? 1 : -1;
+}
+
+__device__ __forceinline__ bool dead(double c, double eps) { return eps > 0.0 && c == 0.0; }
+__device__ __forceinline__ double trunc_c(double c, double eps) {
+  return (eps > 0.0 && !(fabs(c) >= eps)) ? 0.0 : c;
+}
+
+// The FP64 pipe of this GPU issues 2 instructions per cycle per SM, so the
+// gate kernel keeps it for the rotation arithmetic only: zero tests and
+// threshold compares run on the integer bit patterns (for finite doubles,
+// |a| < |b| exactly when (bits(a) & ~sign) < (bits(b) & ~sign) as unsigned).
+constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr uint64_t kSignBit = 0x8000000000000000ull;
+__device__ __forceinline__ uint64_t dbits(double c) { return (uint64_t)__double_as_longlong(c); }
+__device__ __forceinline__ bool is_zero_bits(double c) { return (dbits(c) << 1) == 0ull; }
+__device__ __forceinline__ double with_sign(double c, bool negate) {
+  return __longlong_as_double((long long)(dbits(c) ^ (negate ? kSignBit : 0ull)));
+}
+
+// Births (partners not yet in the table) are staged in shared memory and
+// appended with one atomic per block at the end of a gate; a block whose
+// staging area fills up appends the rest directly, one atomic per warp.
+template <int W>
+struct GateStage {
+  static constexpr int kCap = (W <= 2) ? 512 : 256;
+  uint64_t key[kCap][2 * W];
+  double coef[kCap];
+};
+
+struct GateShared {
+  long long delta[kBlock / 32];
+  unsigned long long ac[kBlock / 32];
+  unsigned nstage;
+  unsigned err;
+  unsigned long long base;
+};
+
+__device__ __forceinline__ double ld_coef(const double* c, uint64_t i) { return __ldcg(c + i); }
+
+// Find key k among the entries that existed when the gate started (dense
+// position < T0); slots of this gate's births are skipped without reading
+// their keys, so births need no fence before they are published.
+template <int W>
+__device__ __forceinline__ int64_t index_find_old(const DevTable& t, const Key<W>& k, uint64_t h,
+                                                  uint32_t tag, uint64_t T0, unsigned& err) {
+  uint64_t pos = h & t.imask;
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    const uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
+    if (s == 0) return -1;
+    if ((uint32_t)(s >> 32) == tag) {
+      const uint32_t idx = (uint32_t)s;
+      if ((uint64_t)idx < T0 && keys_equal(ld_key_cg<W>(t.keys, idx), k)) return (int64_t)idx;
+    }
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+  return -2;
+}
+
+// One gate over the stored entries [0, T0) by one block of a grid (see the
+// file comment).  Births go to dense positions T0 + atomicAdd(cnt_slot).
+// The block's live-count change is added to *dlt_slot and its anticommuting
+// count to ctl->ac_total.  Ends with the block's threads synchronised.
+template <int W>
+__device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const GateArgs& g,
+                                          uint64_t T0, unsigned long long* cnt_slot,
+                                          long long* dlt_slot, GateStage<W>& stage,
+                                          GateShared& sh) {
+  constexpr int kWarps = kBlock / 32;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const bool noise = g.damp != nullptr;
+  const bool use_eps = g.use_eps != 0;
+  const uint64_t eps_bits = g.eps_bits;
+  // liveness and truncation on bit patterns (see kAbsMask)
+  auto is_dead = [&](double c) { return use_eps && is_zero_bits(c); };
+  auto trunc = [&](double c) { return (use_eps && (dbits(c) & kAbsMask) < eps_bits) ? 0.0 : c; };
+  long long delta = 0;
+  unsigned long long n_ac = 0;  // live anticommuting terms (for the byte model)
+  unsigned err = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  // warp-uniform trip count: every lane reaches the ballots below
+  for (uint64_t base = (uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u); base < T0;
+       base += stride) {
+    const uint64_t i = base + lane;
+    bool want = false;
+    double child = 0.0;
+    if (i < T0) {
+      const Key<W> Q = ld_key_cg<W>(t.keys, i);
+      int acnt = 0, kq = 0;
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        acnt += __popcll(g.px[j] & Q.z(j)) + __popcll(g.pz[j] & Q.x(j));
+        if (noise) kq += __popcll((Q.x(j) | Q.z(j)) & g.supp[j]);
+      }
+      if ((acnt & 1) == 0) {
+        if (noise && kq) {  // commuting term: damping only
+          const double c = ld_coef(t.coef, i);
+          if (!is_dead(c)) {
+            const double d = trunc(__dmul_rn(c, g.damp[kq]));
+            delta -= is_dead(d);
+            t.coef[i] = d;
+          }
+        }
+      } else {
+        Key<W> R;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          R.x(j) = Q.x(j) ^ g.px[j];
+          R.z(j) = Q.z(j) ^ g.pz[j];
+        }
+        const double cQ = ld_coef(t.coef, i);
+        const bool liveQ = !is_dead(cQ);
+        uint64_t pw = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) pw |= (Q.x(j) & g.pvx[j]) | (Q.z(j) & g.pvz[j]);
+        // The member of {Q, R} with the pivot bit of P clear owns the pair,
+        // decided from keys only.  A truncated member with the bit set has
+        // nothing to do (its partner either owns the pair or is absent), so it
+        // skips the lookup; a truncated owner still looks up, since a live
+        // partner revives it.
+        int64_t jr = -3;
+        if (liveQ || pw == 0) {
+          const uint64_t h = key_hash(R);
+          jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
+        }
+        n_ac += liveQ;
+        const bool neg = sigma_of<W>(g, Q) < 0;  // i P Q = -R
+        if (jr >= 0) {
+          const double cR = pw == 0 ? ld_coef(t.coef, jr) : 0.0;
+          if (pw == 0 && (liveQ || !is_dead(cR))) {  // this thread owns the pair
+            double dQ = cQ, dR = cR;
+            if (noise) {
+              int kr = 0;
+#pragma unroll
+              for (int j = 0; j < W; ++j) kr += __popcll((R.x(j) | R.z(j)) & g.supp[j]);
+              if (kq) dQ = __dmul_rn(dQ, g.damp[kq]);
+              if (kr) dR = __dmul_rn(dR, g.damp[kr]);
+            }
+            const double sQ = __dmul_rn(g.sth, dQ);  // child of Q lands on R: +-sQ
+            const double sR = __dmul_rn(g.sth, dR);  // child of R lands on Q: -+sR
+            const double nQ = trunc(__dadd_rn(__dmul_rn(g.cth, dQ), with_sign(sR, !neg)));
+            const double nR = trunc(__dadd_rn(__dmul_rn(g.cth, dR), with_sign(sQ, neg)));
+            delta += (long long)!is_dead(nQ) - (long long)liveQ + (long long)!is_dead(nR) -
+                     (long long)!is_dead(cR);
+            t.coef[i] = nQ;
+            t.coef[jr] = nR;
+          }
+        } else if (jr == -1 && liveQ) {
+          const double dQ = (noise && kq) ? __dmul_rn(cQ, g.damp[kq]) : cQ;
+          const double nQ = trunc(__dmul_rn(g.cth, dQ));
+          delta -= is_dead(nQ);
+          t.coef[i] = nQ;
+          child = with_sign(__dmul_rn(g.sth, dQ), neg);
+          want = (g.wmax < 0 || weight(R) <= g.wmax) &&
+                 !(use_eps && (dbits(child) & kAbsMask) < eps_bits);
+        }
+      }
+    }
+    // stage the births of this warp in shared memory (one shared atomic per warp)
+    const unsigned ballot = __ballot_sync(kFull, want);
+    if (ballot) {
+      const int leader = __ffs(ballot) - 1;
+      unsigned b0 = 0;
+      if (lane == leader) b0 = atomicAdd(&sh.nstage, (unsigned)__popc(ballot));
+      b0 = __shfl_sync(kFull, b0, leader);
+      const unsigned pos = b0 + __popc(ballot & ((1u << lane) - 1u));
+      const bool staged = want && pos < (unsigned)GateStage<W>::kCap;
+      const bool direct = want && !staged;
+      Key<W> R;
+      if (want) {
+        const Key<W> Q = ld_key_cg<W>(t.keys, i);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          R.x(j) = Q.x(j) ^ g.px[j];
+          R.z(j) = Q.z(j) ^ g.pz[j];
+        }
+      }
+      if (staged) {
+#pragma unroll
+        for (int j = 0; j < 2 * W; ++j) stage.key[pos][j] = R.w[j];
+        stage.coef[pos] = child;
+      }
+      const unsigned over = __ballot_sync(kFull, direct);
+      if (over) {  // staging area full: append straight away
+        const int ol = __ffs(over) - 1;
+        unsigned long long ob = 0;
+        if (lane == ol) ob = T0 + atomicAdd(cnt_slot, (unsigned long long)__popc(over));
+        ob = __shfl_sync(kFull, ob, ol);
+        if (direct) {
+          const uint64_t idx = ob + __popc(over & ((1u << lane) - 1u));
+          if (idx < t.cap) {
+            st_key<W>(t.keys, idx, R);
+            t.coef[idx] = child;
+            const uint64_t h = key_hash(R);
+            index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+          } else {
+            err |= kErrAppend;
+          }
+        }
+      }
+      delta += want;
+    }
+  }
+  // the next kernel on the stream may now be scheduled (it waits for this grid)
+  asm volatile("griddepcontrol.launch_dependents;");
+
+  __syncthreads();
+  const unsigned nst = min(sh.nstage, (unsigned)GateStage<W>::kCap);
+  if (nst) {
+    if (threadIdx.x == 0) sh.base = T0 + atomicAdd(cnt_slot, (unsigned long long)nst);
+    __syncthreads();
+    // births are never looked up by the gate that creates them, so their
+    // keys and index slots need no ordering between each other
+    for (unsigned k = threadIdx.x; k < nst; k += kBlock) {
+      const uint64_t idx = sh.base + k;
+      if (idx < t.cap) {
+        Key<W> R;
+#pragma unroll
+        for (int j = 0; j < 2 * W; ++j) R.w[j] = stage.key[k][j];
+        st_key<W>(t.keys, idx, R);
+        t.coef[idx] = stage.coef[k];
+        const uint64_t h = key_hash(R);
+        index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+      } else {
+        err |= kErrAppend;
+      }
+    }
+  }
+
+  delta = warp_sum(delta);
+  n_ac = warp_sum(n_ac);
+  if (lane == 0) {
+    sh.delta[warp] = delta;
+    sh.ac[warp] = n_ac;
+  }
+  if (err) atomicOr(&sh.err, err);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long d = 0;
+    unsigned long long a = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      d += sh.delta[w];
+      a += sh.ac[w];
+    }
+    // fire-and-forget reductions: no block waits for another
+    if (d) atomicAdd(reinterpret_cast<unsigned long long*>(dlt_slot), (unsigned long long)d);
+    if (a) atomicAdd(&ctl->ac_total, a);
+    if (sh.err) atomicOr(&ctl->error, sh.err);
+    sh.nstage = 0;
+    sh.err = 0;
+  }
+  __syncthreads();
+}
+
+// One kernel per gate (the graph / PDL path).  Gate g reads its input size
+// from slot (g+2)%3 of the control block, which gate g-1 finished writing.
+template <int W>
+__global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict__ tabp,
+                                                      DevCtl* __restrict__ ctl, GateArgs g) {
+  __shared__ GateStage<W> stage;
+  __shared__ GateShared sh;
+  const unsigned gid = g.gate_id;
+  const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
+  // With programmatic dependent launch this kernel may already be resident
+  // while the previous gate finishes; wait for its results first.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const DevTable t = *tabp;
+  // every thread reads the (final) state left by the previous gate
+  const unsigned long long T0 = __ldcg(&ctl->base[prev]) + __ldcg(&ctl->cnt[prev]);
+  const long long L0 = __ldcg(&ctl->live_base[prev]) + __ldcg(&ctl->dlt[prev]);
+  bool run = (gid >= __ldcg(&ctl->first_gate)) && (__ldcg(&ctl->stall) == 0u) &&
+             (__ldcg(&ctl->error) == 0u);
+  const bool room = 2ull * T0 <= t.cap;
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && run && !room) ctl->stall = gid + 1;  // every block skips
+    if (blockIdx.x == 0 && run && room) {
+      ctl->base[slot] = T0;
+      ctl->live_base[slot] = L0;
+      ctl->cnt[next] = 0;
+      ctl->dlt[next] = 0;
+      atomicAdd(&ctl->updates, (double)L0);
+      atomicAdd(&ctl->gates_done, 1ull);
+    }
+    sh.nstage = 0;
+    sh.err = 0;
+  }
+  run = run && room;
+  if (!run) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    return;
+  }
+  __syncthreads();
+  gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, sh);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+constexpr unsigned kBarrierSpinLimit = 1u << 24;
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident): every
+// block adds 1 to a counter that only grows during the launch (release) and
+// waits until it reaches (barrier number) x (blocks) (acquire).  The wait is
+// bounded: on timeout the error bit is set and false is returned.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_ok) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    red_release_add(&ctl->bar_root, 1u);
+    unsigned spins = 0;
+    while ((int)(ld_acquire_u32(&ctl->bar_root) - target) < 0) {
+      if (++spins > kBarrierSpinLimit) {
+        ok = 0;
+        atomicOr(&ctl->error, kErrTimeout);
+        break;
+      }
+      __nanosleep(16);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// All gates of a layer in one cooperative launch: the table size travels in
+// registers and consecutive gates are separated by a grid barrier instead of
+// a kernel boundary.  Gate ids, slots and the capacity stall are the same as
+// for gate_kernel, so chain_init / chain_finish serve both.
+template <int W>
+__global__ void __launch_bounds__(kBlock, (W == 1) ? 5 : ((W == 2) ? 3 : 2))
+    layer_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
+                 const GateArgs* __restrict__ gates, unsigned n_gates) {
+  __shared__ GateStage<W> stage;
+  __shared__ GateShared sh;
+  __shared__ GateArgs s_gate[2];  // current gate and the prefetched next one
+  __shared__ int s_ok;
+  const DevTable t = *tabp;
+  const unsigned first = __ldcg(&ctl->first_gate);
+  const int q0 = (int)((first + 2u) % 3u);
+  unsigned long long T0 = __ldcg(&ctl->base[q0]) + __ldcg(&ctl->cnt[q0]);
+  long long L0 = __ldcg(&ctl->live_base[q0]) + __ldcg(&ctl->dlt[q0]);
+  unsigned target = 0;  // barrier counter value to wait for (cleared by chain_init)
+  if (threadIdx.x == 0) {
+    sh.nstage = 0;
+    sh.err = 0;
+  }
+  auto fetch_args = [&](unsigned gid, int buf) {
+    const unsigned* src = reinterpret_cast<const unsigned*>(gates + gid);
+    unsigned* dst = reinterpret_cast<unsigned*>(&s_gate[buf]);
+    for (unsigned k = threadIdx.x; k < sizeof(GateArgs) / 4; k += kBlock) dst[k] = __ldg(src + k);
+  };
+  if (__ldcg(&ctl->stall) != 0u || __ldcg(&ctl->error) != 0u) return;  // uniform
+  if (first < n_gates) fetch_args(first, 0);
+  for (unsigned gid = first; gid < n_gates; ++gid) {
+    const int slot = (int)(gid % 3u), next = (int)((gid + 1u) % 3u);
+    const int buf = (int)((gid - first) & 1u);
+    if (2ull * T0 > t.cap) {  // the same decision in every block
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->stall = gid + 1;
+      break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->base[slot] = T0;
+      ctl->live_base[slot] = L0;
+      ctl->cnt[next] = 0;
+      ctl->dlt[next] = 0;
+      atomicAdd(&ctl->updates, (double)L0);
+      atomicAdd(&ctl->gates_done, 1ull);
+    }
+    __syncthreads();  // s_gate[buf] complete
+    gate_pass<W>(t, ctl, s_gate[buf], T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, sh);
+    if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);  // overlaps the barrier wait
+    if (!grid_sync(ctl, target, s_ok)) return;
+    T0 += __ldcg(&ctl->cnt[slot]);
+    L0 += __ldcg(&ctl->dlt[slot]);
+    if (__ldcg(&ctl->error) != 0u) return;  // uniform after the barrier
+  }
+}
+
+__global__ void chain_init_kernel(DevCtl* ctl, unsigned first_gate) {
+  const int q = (int)((first_gate + 2u) % 3u), p = (int)(first_gate % 3u);
+  ctl->bar_root = 0;
+  ctl->base[q] = ctl->n_terms;
+  ctl->live_base[q] = ctl->n_live;
+  ctl->cnt[q] = 0;
+  ctl->dlt[q] = 0;
+  ctl->cnt[p] = 0;
+  ctl->dlt[p] = 0;
+  ctl->stall = 0;
+  ctl->first_gate = first_gate;
+}
+
+__global__ void chain_finish_kernel(DevCtl* ctl, unsigned n_gates) {
+  const unsigned end = ctl->stall ? ctl->stall - 1u : n_gates;  // first gate not applied
+  const int q = (int)((end + 2u) % 3u);                         // slot of gate end-1
+  ctl->n_terms = ctl->base[q] + ctl->cnt[q];
+  ctl->n_live = ctl->live_base[q] + ctl->dlt[q];
+}
+
+// -------------------------------------------------- canonicalisation
+
+// Digit word of Def. "Lowest integer representation": bit 2q = x_q ^ z_q,
+// bit 2q+1 = z_q, so the 2-bit digit of qubit q is I=0, X=1, Y=2, Z=3.
+__device__ __forceinline__ uint64_t spread32(uint32_t a) {
+  uint64_t x = a;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t compact64(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+__device__ __forceinline__ uint64_t digits32(uint32_t x, uint32_t z) {
+  return spread32(x ^ z) | (spread32(z) << 1);
+}
+
+// Z_n (Algorithm 2): min over the n translations of the 2n-bit digit integer.
+// T^j moves the letter of qubit q+j to qubit q, i.e. rotates the integer
+// right by 2j bits inside 2n bits.
+__device__ __forceinline__ void canon_zn_w1(Key<1>& k, int n) {
+  const uint64_t x = k.x(0), z = k.z(0);
+  if (n <= 32) {
+    const int nb = 2 * n;
+    const uint64_t mask = (nb == 64) ? ~0ull : ((1ull << nb) - 1ull);
+    const uint64_t v = digits32((uint32_t)x, (uint32_t)z);
+    uint64_t best = v;
+    for (int j = 1; j < n; ++j) {
+      const uint64_t r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
+      best = r < best ? r : best;
+    }
+    const uint32_t zz = compact64(best >> 1);
+    const uint32_t xz = compact64(best);
+    k.x(0) = (uint64_t)(xz ^ zz);
+    k.z(0) = (uint64_t)zz;
+    return;
+  }
+  typedef unsigned __int128 u128;
+  const int nb = 2 * n;
+  const u128 mask = (nb == 128) ? ~(u128)0 : (((u128)1 << nb) - 1);
+  const u128 v = (u128)digits32((uint32_t)x, (uint32_t)z) |
+                 ((u128)digits32((uint32_t)(x >> 32), (uint32_t)(z >> 32)) << 64);
+  u128 best = v;
+  for (int j = 1; j < n; ++j) {
+    const u128 r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
+    best = r < best ? r : best;
+  }
+  const uint64_t lo = (uint64_t)best, hi = (uint64_t)(best >> 64);
+  const uint64_t zz = (uint64_t)compact64(lo >> 1) | ((uint64_t)compact64(hi >> 1) << 32);
+  const uint64_t xz = (uint64_t)compact64(lo) | ((uint64_t)compact64(hi) << 32);
+  k.x(0) = xz ^ zz;
+  k.z(0) = zz;
+}
+
+template <int W>
+__device__ __forceinline__ int digit_at(const Key<W>& k, int q) {
+  const int xb = (int)((k.x(q >> 6) >> (q & 63)) & 1ull);
+  const int zb = (int)((k.z(q >> 6) >> (q & 63)) & 1ull);
+  return (zb << 1) | (xb ^ zb);
+}
+
+// Multi-word Z_n: compare translations digit by digit from the most
+// significant qubit and keep the smallest.
+template <int W>
+__device__ __forceinline__ void canon_zn_generic(Key<W>& k, int n) {
+  int best = 0;
+  for (int j = 1; j < n; ++j) {
+    int cmp = 0;
+    for (int q = n - 1; q >= 0 && cmp == 0; --q) {
+      int qa = q + j;
+      qa -= (qa >= n) ? n : 0;
+      int qb = q + best;
+      qb -= (qb >= n) ? n : 0;
+      const int a = digit_at<W>(k, qa), b = digit_at<W>(k, qb);
+      cmp = (a < b) ? -1 : ((a > b) ? 1 : 0);
+    }
+    if (cmp < 0) best = j;
+  }
+  if (best == 0) return;
+  Key<W> r;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
+  for (int q = 0; q < n; ++q) {
+    int src = q + best;
+    src -= (src >= n) ? n : 0;
+    const uint64_t xb = (k.x(src >> 6) >> (src & 63)) & 1ull;
+    const uint64_t zb = (k.z(src >> 6) >> (src & 63)) & 1ull;
+    r.x(q >> 6) |= xb << (q & 63);
+    r.z(q >> 6) |= zb << (q & 63);
+  }
+  k = r;
+}
+
+__device__ __forceinline__ uint64_t range_word(int w, int lo, int hi) {
+  int a = lo - 64 * w, b = hi - 64 * w;
+  a = a < 0 ? 0 : a;
+  b = b > 64 ? 64 : b;
+  if (b <= a) return 0ull;
+  const uint64_t upto_b = (b == 64) ? ~0ull : ((1ull << b) - 1ull);
+  const uint64_t below_a = (1ull << a) - 1ull;  // a < 64 here
+  return upto_b & ~below_a;
+}
+
+// S_n (Algorithm 3): count n_X, n_Y, n_Z and write Z^{nZ} Y^{nY} X^{nX} I...
+template <int W>
+__device__ __forceinline__ void canon_sn(Key<W>& k) {
+  int nx = 0, ny = 0, nz = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    nx += __popcll(k.x(j) & ~k.z(j));
+    ny += __popcll(k.x(j) & k.z(j));
+    nz += __popcll(k.z(j) & ~k.x(j));
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    k.z(j) = range_word(j, 0, nz + ny);
+    k.x(j) = range_word(j, nz, nz + ny + nx);
+  }
+}
+
+template <int W, int G>
+__device__ __forceinline__ void canon(Key<W>& k, int n) {
+  if constexpr (G == 1) {
+    if constexpr (W == 1) {
+      canon_zn_w1(k, n);
+    } else {
+      canon_zn_generic<W>(k, n);
+    }
+  } else if constexpr (G == 2) {
+    canon_sn<W>(k);
+  }
+}
+
+// ------------------------------------------------------ merge / insert
+
+template <int W, int G>
+__global__ void __launch_bounds__(kBlock)
+    merge_insert_kernel(const uint64_t* __restrict__ src_keys, const double* __restrict__ src_coef,
+                        uint64_t count, const unsigned long long* count_dev, int skip_zero,
+                        int wmax, int n, DevTable dst, DevCtl* ctl) {
+  const uint64_t T = count_dev ? *count_dev : count;
+  unsigned err = 0;
+  unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    const double c = src_coef[i];
+    if (skip_zero && c == 0.0) continue;
+    Key<W> K = ld_key<W>(src_keys, i);
+    if (wmax >= 0 && weight(K) > wmax) continue;
+    canon<W, G>(K, n);
+    const uint64_t h = key_hash(K);
+    const uint32_t tag = tag_of(h);
+    uint64_t pos = h & dst.imask;
+    bool done = false;
+    for (uint64_t probe = 0; probe <= dst.imask; ++probe) {
+      unsigned long long s = __ldcg(index + pos);
+      if (s == 0ull) {
+        const unsigned long long mine = ((unsigned long long)tag << 32) | kPendingIdx;
+        const unsigned long long old = atomicCAS(index + pos, 0ull, mine);
+        if (old == 0ull) {
+          cg::coalesced_group grp = cg::coalesced_threads();
+          unsigned long long b0 = 0;
+          if (grp.thread_rank() == 0) b0 = atomicAdd(&ctl->n_next, (unsigned long long)grp.size());
+          b0 = grp.shfl(b0, 0);
+          const unsigned long long idx = b0 + grp.thread_rank();
+          if (idx >= dst.cap) {
+            err |= kErrAppend;
+          } else {
+            st_key<W>(dst.keys, idx, K);
+            dst.coef[idx] = c;
+            __threadfence();
+            atomicExch(index + pos, ((unsigned long long)tag << 32) | idx);
+          }
+          done = true;
+          break;
+        }
+        s = old;
+      }
+      if ((uint32_t)(s >> 32) == tag) {
+        int spins = 0;
+        while ((uint32_t)s == kPendingIdx && spins < kSpinLimit) {
+          ++spins;
+          __nanosleep(64);
+          s = *reinterpret_cast<volatile unsigned long long*>(index + pos);
+        }
+        if ((uint32_t)s == kPendingIdx) {
+          err |= kErrTimeout;
+          done = true;
+          break;
+        }
+        const uint32_t idx = (uint32_t)s;
+        if (keys_equal(ld_key_cg<W>(dst.keys, idx), K)) {
+          atomicAdd(dst.coef + idx, c);
+          done = true;
+          break;
+        }
+      }
+      pos = (pos + 1) & dst.imask;
+    }
+    if (!done) err |= kErrProbe;
+  }
+  if (err) atomicOr(&ctl->error, err);
+}
+
+// Coefficient truncation of the merged entries and live count.
+__global__ void __launch_bounds__(kBlock) finalize_kernel(DevTable t, DevCtl* ctl, double eps) {
+  __shared__ long long s_live[kBlock / 32];
+  const uint64_t T = *reinterpret_cast<volatile unsigned long long*>(&ctl->n_next);
+  long long live = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    if (eps > 0.0) {
+      const double c = t.coef[i];
+      if (c != 0.0 && !(fabs(c) >= eps)) {
+        t.coef[i] = 0.0;
+      } else {
+        live += (c != 0.0);
+      }
+    } else {
+      live += 1;
+    }
+  }
+  live = warp_sum(live);
+  if ((threadIdx.x & 31) == 0) s_live[threadIdx.x >> 5] = live;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int w = 0; w < kBlock / 32; ++w) s += s_live[w];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live), (unsigned long long)s);
+  }
+}
+
+// Copy kept entries into a fresh table (unique keys).  extra_eps / extra_wmax
+// implement pp_truncate on top of the context's own rule.
+template <int W>
+__global__ void __launch_bounds__(kBlock)
+    compact_kernel(DevTable src, uint64_t count, DevTable dst, int with_index, double eps,
+                   double extra_eps, int extra_wmax, DevCtl* ctl) {
+  const int lane = threadIdx.x & 31;
+  unsigned err = 0;
+  long long live = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count;
+       base += stride) {
+    const uint64_t i = base + lane;
+    bool keep = false;
+    Key<W> K;
+    double c = 0.0;
+    if (i < count) {
+      c = src.coef[i];
+      keep = !dead(c, eps);
+      if (keep && extra_eps > 0.0 && !(fabs(c) >= extra_eps)) keep = false;
+      if (keep) {
+        K = ld_key<W>(src.keys, i);
+        if (extra_wmax >= 0 && weight(K) > extra_wmax) keep = false;
+      }
+    }
+    const unsigned ballot = __ballot_sync(kFull, keep);
+    if (ballot) {
+      const int leader = __ffs(ballot) - 1;
+      unsigned long long b0 = 0;
+      if (lane == leader) b0 = atomicAdd(&ctl->n_next, (unsigned long long)__popc(ballot));
+      b0 = __shfl_sync(kFull, b0, leader);
+      if (keep) {
+        const uint64_t idx = b0 + __popc(ballot & ((1u << lane) - 1u));
+        if (idx >= dst.cap) {
+          err |= kErrAppend;
+        } else {
+          st_key<W>(dst.keys, idx, K);
+          dst.coef[idx] = c;
+          ++live;
+          if (with_index) {
+            const uint64_t h = key_hash(K);
+            index_claim(dst, h & dst.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+          }
+        }
+      }
+    }
+  }
+  live = warp_sum(live);
+  if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live), (unsigned long long)live);
+  if (err) atomicOr(&ctl->error, err);
+}
+
+template <int W, int G>
+__global__ void __launch_bounds__(kBlock)
+    canon_inplace_kernel(uint64_t* keys, const uint64_t* keys_in, uint64_t count, int n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    Key<W> k = ld_key_cg<W>(keys_in, i);
+    canon<W, G>(k, n);
+    st_key<W>(keys, i, k);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock)
+    damp_layer_kernel(DevTable t, DevCtl* ctl, const double* table, double eps) {
+  __shared__ long long s_d[kBlock / 32];
+  const uint64_t T = *reinterpret_cast<volatile unsigned long long*>(&ctl->n_terms);
+  long long delta = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    const double c = t.coef[i];
+    if (dead(c, eps)) continue;
+    const int w = weight(ld_key<W>(t.keys, i));
+    if (w == 0) continue;
+    const double d = trunc_c(__dmul_rn(c, table[w]), eps);
+    if (dead(d, eps)) --delta;
+    t.coef[i] = d;
+  }
+  delta = warp_sum(delta);
+  if ((threadIdx.x & 31) == 0) s_d[threadIdx.x >> 5] = delta;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int w = 0; w < kBlock / 32; ++w) s += s_d[w];
+    if (s) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live), (unsigned long long)s);
+  }
+}
+
+// ------------------------------------------------------------- overlap
+
+template <int W>
+__device__ __forceinline__ double overlap_plain(const Key<W>& k, const OverlapArgs& a) {
+  if (a.basis) {
+    uint64_t xo = 0;
+    int par = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      xo |= k.x(j);
+      par += __popcll(k.z(j) & a.bits[j]);
+    }
+    if (xo) return 0.0;
+    return (par & 1) ? -1.0 : 1.0;
+  }
+  double v = 1.0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    uint64_t m = k.x(j) | k.z(j);
+    while (m) {
+      const int b = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      const int q = 64 * j + b;
+      const int xb = (int)((k.x(j) >> b) & 1ull), zb = (int)((k.z(j) >> b) & 1ull);
+      const int l = xb ? (zb ? 1 : 0) : 2;  // X -> 0, Y -> 1, Z -> 2
+      v *= a.bloch[3 * q + l];
+    }
+  }
+  return v;
+}
+
+// Average of Tr[rho T^j r] over the n translations.
+template <int W>
+__device__ __forceinline__ double overlap_zn(const Key<W>& k, const OverlapArgs& a) {
+  const int n = a.n;
+  double acc = 0.0;
+  if (a.basis) {
+    uint64_t xo = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) xo |= k.x(j);
+    if (xo) return 0.0;
+    for (int s = 0; s < n; ++s) {
+      int par = 0;
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        uint64_t m = k.z(j);
+        while (m) {
+          const int b = __ffsll((long long)m) - 1;
+          m &= m - 1;
+          int q = 64 * j + b - s;
+          q += (q < 0) ? n : 0;
+          par += (int)((a.bits[q >> 6] >> (q & 63)) & 1ull);
+        }
+      }
+      acc += (par & 1) ? -1.0 : 1.0;
+    }
+    return acc / (double)n;
+  }
+  for (int s = 0; s < n; ++s) {
+    double v = 1.0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      uint64_t m = k.x(j) | k.z(j);
+      while (m) {
+        const int b = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        int q = 64 * j + b - s;
+        q += (q < 0) ? n : 0;
+        const int xb = (int)((k.x(j) >> b) & 1ull), zb = (int)((k.z(j) >> b) & 1ull);
+        const int l = xb ? (zb ? 1 : 0) : 2;
+        v *= a.bloch[3 * q + l];
+      }
+    }
+    acc += v;
+  }
+  return acc / (double)n;
+}
+
+template <int W>
+__device__ __forceinline__ double overlap_sn(const Key<W>& k, const OverlapArgs& a) {
+  int nx = 0, ny = 0, nz = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    nx += __popcll(k.x(j) & ~k.z(j));
+    ny += __popcll(k.x(j) & k.z(j));
+    nz += __popcll(k.z(j) & ~k.x(j));
+  }
+  const int S = a.n + 1;
+  return a.sn_table[((size_t)nx * S + ny) * S + nz];
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock)
+    overlap_kernel(const uint64_t* __restrict__ keys, const double* __restrict__ coef,
+                   uint64_t count, const unsigned long long* count_dev, OverlapArgs a,
+                   double* partials) {
+  __shared__ double s_acc[kBlock / 32];
+  const uint64_t T = count_dev ? *count_dev : count;
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
+    const double c = coef[i];
+    if (c == 0.0) continue;
+    const Key<W> k = ld_key<W>(keys, i);
+    double ov;
+    if (a.group == 1)
+      ov = overlap_zn<W>(k, a);
+    else if (a.group == 2)
+      ov = overlap_sn<W>(k, a);
+    else
+      ov = overlap_plain<W>(k, a);
+    acc += c * ov;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += s_acc[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) reduce_partials_kernel(const double* partials, int m,
+                                                                double* out) {
+  __shared__ double s_acc[kBlock / 32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) acc += partials[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += s_acc[w];
+    out[0] = s;
+  }
+}
+
+// Orbit average of Tr[rho g.s] over S_n as a function of (n_X, n_Y, n_Z):
+// sites are filled in order, site k drawing each remaining letter with
+// probability (remaining count) / (remaining sites).  E_k over states
+// (x, y, z) of remaining counts; every step is a convex combination.
+__global__ void __launch_bounds__(1024) sn_table_kernel(int n, const double* bloch, double* table,
+                                                       double* work) {
+  const int S = n + 1;
+  const size_t total = (size_t)S * S * S;
+  // after n steps the result must sit in `table`: start in whichever buffer
+  // makes the last write land there
+  double* nxt = (n & 1) ? work : table;
+  double* cur = (n & 1) ? table : work;
+  for (size_t i = threadIdx.x; i < total; i += blockDim.x) nxt[i] = (i == 0) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = n - 1; k >= 0; --k) {
+    const int left = n - k;
+    const double bX = bloch[3 * k], bY = bloch[3 * k + 1], bZ = bloch[3 * k + 2];
+    for (size_t f = threadIdx.x; f < total; f += blockDim.x) {
+      const int z = (int)(f % S), y = (int)((f / S) % S), x = (int)(f / ((size_t)S * S));
+      double v = 0.0;
+      if (x + y + z <= left) {
+        const int iI = left - x - y - z;
+        if (iI > 0) v += (double)iI * nxt[f];
+        if (x > 0) v += (double)x * bX * nxt[f - (size_t)S * S];
+        if (y > 0) v += (double)y * bY * nxt[f - S];
+        if (z > 0) v += (double)z * bZ * nxt[f - 1];
+        v /= (double)left;
+      }
+      cur[f] = v;
+    }
+    __syncthreads();
+    double* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+// x [m][W], z [m][W] -> keys [m][2W]; flags strings with bits at or above n.
+template <int W>
+__global__ void __launch_bounds__(kBlock)
+    pack_keys_kernel(const uint64_t* __restrict__ x, const uint64_t* __restrict__ z, uint64_t m,
+                     int n, uint64_t* keys, unsigned* bad) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    Key<W> k;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      k.x(j) = x[i * W + j];
+      k.z(j) = z[i * W + j];
+      const int lo = 64 * j;
+      const uint64_t valid = (n >= lo + 64) ? ~0ull : ((n > lo) ? ((1ull << (n - lo)) - 1ull) : 0ull);
+      ok &= ((k.x(j) | k.z(j)) & ~valid) == 0ull;
+    }
+    st_key<W>(keys, i, k);
+    if (!ok) atomicOr(bad, 1u);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+#define PP_DISPATCH_W(W, ...)                     \
+  switch (W) {                                    \
+    case 1: { constexpr int WW = 1; __VA_ARGS__; break; } \
+    case 2: { constexpr int WW = 2; __VA_ARGS__; break; } \
+    case 3: { constexpr int WW = 3; __VA_ARGS__; break; } \
+    case 4: { constexpr int WW = 4; __VA_ARGS__; break; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate) {
+  chain_init_kernel<<<1, 1, 0, s>>>(ctl, first_gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_finish(cudaStream_t s, DevCtl* ctl, unsigned n_gates) {
+  chain_finish_kernel<<<1, 1, 0, s>>>(ctl, n_gates);
+  return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_gate_w(int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                          const GateArgs& g, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, gate_kernel<W>, tab, ctl, g);
+}
+
+template <int W>
+cudaError_t launch_layer_w(int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                           const GateArgs* gates, unsigned n_gates) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, layer_kernel<W>, tab, ctl, gates, n_gates);
+}
+
+cudaError_t launch_layer(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                         const GateArgs* gates, unsigned n_gates) {
+  switch (W) {
+    case 1: return launch_layer_w<1>(grid, s, tab, ctl, gates, n_gates);
+    case 2: return launch_layer_w<2>(grid, s, tab, ctl, gates, n_gates);
+    case 3: return launch_layer_w<3>(grid, s, tab, ctl, gates, n_gates);
+    case 4: return launch_layer_w<4>(grid, s, tab, ctl, gates, n_gates);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int layer_blocks_per_sm(int W) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (W) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<1>, kBlock, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<2>, kBlock, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<3>, kBlock, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<4>, kBlock, 0); break;
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 0;
+}
+
+cudaError_t launch_gate(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
+                        const GateArgs& g, bool pdl) {
+  switch (W) {
+    case 1: return launch_gate_w<1>(grid, s, tab, ctl, g, pdl);
+    case 2: return launch_gate_w<2>(grid, s, tab, ctl, g, pdl);
+    case 3: return launch_gate_w<3>(grid, s, tab, ctl, g, pdl);
+    case 4: return launch_gate_w<4>(grid, s, tab, ctl, g, pdl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cudaStream_t s,
+                                  const uint64_t* src_keys, const double* src_coef,
+                                  uint64_t count, const unsigned long long* count_dev,
+                                  int skip_zero, DevTable dst, DevCtl* ctl) {
+  switch (group) {
+    case 0:
+      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 0><<<grid, kBlock, 0, s>>>(
+                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
+      break;
+    case 1:
+      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 1><<<grid, kBlock, 0, s>>>(
+                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
+      break;
+    case 2:
+      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 2><<<grid, kBlock, 0, s>>>(
+                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps) {
+  finalize_kernel<<<grid, kBlock, 0, s>>>(dst, ctl, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(int W, int grid, cudaStream_t s, DevTable src, uint64_t count,
+                           DevTable dst, int with_index, double eps, double extra_eps,
+                           int extra_wmax, DevCtl* ctl_dst) {
+  PP_DISPATCH_W(W, (compact_kernel<WW><<<grid, kBlock, 0, s>>>(src, count, dst, with_index, eps,
+                                                               extra_eps, extra_wmax, ctl_dst)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_canon_inplace(int W, int group, int n, int grid, cudaStream_t s,
+                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count) {
+  if (group == 1) {
+    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 1><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
+  } else if (group == 2) {
+    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 2><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
+  } else {
+    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 0><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_damp_layer(int W, int grid, cudaStream_t s, DevTable t, DevCtl* ctl,
+                              const double* table, double eps) {
+  PP_DISPATCH_W(W, (damp_layer_kernel<WW><<<grid, kBlock, 0, s>>>(t, ctl, table, eps)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap(int W, int grid, cudaStream_t s, const uint64_t* keys,
+                           const double* coef, uint64_t count,
+                           const unsigned long long* count_dev, const OverlapArgs& a,
+                           double* partials, double* out) {
+  PP_DISPATCH_W(W, (overlap_kernel<WW><<<grid, kBlock, 0, s>>>(keys, coef, count, count_dev, a,
+                                                               partials)));
+  reduce_partials_kernel<<<1, kBlock, 0, s>>>(partials, grid, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sn_table(int n, cudaStream_t s, const double* bloch, double* work,
+                            double* table) {
+  sn_table_kernel<<<1, 1024, 0, s>>>(n, bloch, table, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_keys(int W, int n, int grid, cudaStream_t s, const uint64_t* x,
+                             const uint64_t* z, uint64_t m, uint64_t* keys, unsigned* bad) {
+  PP_DISPATCH_W(W, (pack_keys_kernel<WW><<<grid, kBlock, 0, s>>>(x, z, m, n, keys, bad)));
+  return cudaGetLastError();
+}
+
+int gate_blocks_per_sm(int W) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (W) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gate_kernel<1>, kBlock, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gate_kernel<2>, kBlock, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gate_kernel<3>, kBlock, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gate_kernel<4>, kBlock, 0); break;
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 4;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+}  // namespace ppk

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every entry point of include/pp.h.
+
+No compute call is made here (no GPU); only host-side argument validation,
+which returns before any CUDA call, is exercised.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2512_12094_gb300 as pp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pp.build()
+    return pp.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pp_[a-z_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == sorted(pp.EXPORTED)
+
+
+def test_exports_via_nm(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", pp._LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pp_[a-z_]+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_config_default(lib):
+    cfg = pp.pp_config_default()
+    assert cfg.batch == 1 and cfg.max_weight == -1 and cfg.use_graphs == 1
+    assert cfg.check_symmetry == 1 and cfg.coeff_eps == 0.0
+
+
+@pytest.mark.parametrize("field,value", [("n_qubits", 0), ("n_qubits", 257), ("batch", 2),
+                                         ("symmetry", 3), ("coef_type", 1),
+                                         ("coeff_eps", -1.0), ("noise_mode", 7)])
+def test_create_rejects_bad_config_without_gpu(lib, field, value):
+    cfg = pp.pp_config_default(n_qubits=8)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    st = lib.pp_create(ctypes.byref(cfg), 0, None, None, None, ctypes.byref(h))
+    assert st == 1  # PP_ERR_ARG
+    assert h.value is None
+    assert lib.pp_last_error().decode() != ""
+
+
+def test_stateless_calls_validate_arguments(lib):
+    assert lib.pp_canonical_keys(0, 1, 1, None, None, None) == 1
+    assert lib.pp_canonical_keys(8, 5, 1, None, None, None) == 1
+    assert lib.pp_canonical_keys(8, 1, 0, None, None, None) == 0  # empty: nothing to do
+    m = ctypes.c_int64(7)
+    assert lib.pp_merge_terms(8, 0, 0, None, None, None, None, ctypes.byref(m), None) == 0
+    assert m.value == 0
+    assert lib.pp_overlap_sum(8, 0, 1, None, None, None, None, None) == 1
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.pp_destroy(None) == 0
+    for name in ("pp_canonicalize", "pp_merge", "pp_synchronize"):
+        assert getattr(lib, name)(None) == 1
+    assert lib.pp_truncate(None, 0.0, -1) == 1
