@@ -218,6 +218,32 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* keys,
                          const double* coef, const double* bloch, double* out, void* stream);
 
+/* pp_merge_terms without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run -- a serving loop whose memory is fixed at
+ * start-up, a thread capturing work into a CUDA graph, or an application that
+ * owns every allocation itself.  The result is the same as pp_merge_terms
+ * (distinct strings in keys_out, FP64 sums in coef_out, unspecified order),
+ * but:
+ *  - the count is written to *m_out_dev, a DEVICE pointer owned by the
+ *    caller (-1 if a device-side check failed), and the call returns as soon
+ *    as the work is queued on `stream` (nothing is synchronised);
+ *  - the hash index and control block live in one static device array of
+ *    about 8 MiB that the library keeps on every device where it is used
+ *    until the process exits, so m is limited to 524288 terms (PP_ERR_ARG
+ *    with a message beyond that);
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - all calls on a device share the array: calls whose work overlaps on
+ *    the device race and must be serialised by the caller.  Each call clears
+ *    what it uses before using it.
+ * No cudaMalloc, cudaMallocAsync, cudaFree or allocating library routine is
+ * called. */
+pp_status pp_merge_terms_noalloc(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                                 const double* coef_in, uint64_t* keys_out, double* coef_out,
+                                 int64_t* m_out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _LIB = os.path.join(_HERE, "libpp.so")
-_SOURCES = ["pp_kernels.cu", "pp_api.cu"]
+_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -124,6 +124,8 @@ _SIGS = {
     "pp_canonical_keys": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp],
     "pp_merge_terms": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _i64p, _vp],
     "pp_overlap_sum": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp],
+    "pp_merge_terms_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                               _vp],
 }
 _RESTYPE = {"pp_last_error": ctypes.c_char_p}
 
@@ -293,6 +295,14 @@ def pp_merge_terms(n_qubits: int, symmetry: int, m: int, keys_in, coef_in, keys_
 def pp_overlap_sum(n_qubits: int, symmetry: int, m: int, keys, coef, bloch, out, stream=None):
     _check(load().pp_overlap_sum(n_qubits, symmetry, int(m), _ptr(keys), _ptr(coef), _ptr(bloch),
                                  _ptr(out), _stream(stream)))
+
+
+def pp_merge_terms_noalloc(n_qubits: int, symmetry: int, m: int, keys_in, coef_in, keys_out,
+                           coef_out, m_out_dev, stream=None):
+    """Queue the allocation-free merge; the count lands in m_out_dev (device int64)."""
+    _check(load().pp_merge_terms_noalloc(n_qubits, symmetry, int(m), _ptr(keys_in), _ptr(coef_in),
+                                         _ptr(keys_out), _ptr(coef_out), _ptr(m_out_dev),
+                                         _stream(stream)))
 
 
 def _stream(s):

@@ -31,6 +31,12 @@ pp_status fail(pp_status st, const std::string& msg) {
   return st;
 }
 
+}  // namespace
+
+void ppk::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
 pp_status cuda_fail(cudaError_t e, const char* where) {
   std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
   if (e == cudaErrorMemoryAllocation) return fail(PP_ERR_OOM, msg);

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 namespace ppk {
 
@@ -151,6 +152,9 @@ cudaError_t launch_sn_table(int n, cudaStream_t s, const double* bloch, double* 
 // bits at or above n.
 cudaError_t launch_pack_keys(int W, int n, int grid, cudaStream_t s, const uint64_t* x,
                              const uint64_t* z, uint64_t m, uint64_t* keys, unsigned* bad);
+
+// Message returned by pp_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 int device_sm_count();
 int gate_blocks_per_sm(int W);  // resident gate-kernel blocks per SM
