@@ -290,6 +290,43 @@ def cpu_baseline(seconds=20.0):
                       "%.1f s CPU, %.3g updates" % (done[0], done[1], total_t, total_upd)}
 
 
+def profile_layer(args):
+    """Run the Z_n-merged job once and bracket layer K (application order)
+    with cudaProfilerStart/Stop, so that `ncu --profile-from-start off`
+    captures exactly that layer's kernels.  Prints the layer's algorithmic
+    bytes (same model as the roofline) for comparison with ncu's counters."""
+    import torch
+    import paper_2512_12094_gb300 as pp
+    pp.build()
+    pp.load()
+    wl = pi.config1_ring()
+    ox, oz, oc = wl.observable.arrays()
+    cfg = pp.pp_config_default(n_qubits=32, symmetry=pp.SYM_ZN, coeff_eps=wl.eps,
+                               max_weight=wl.max_weight, profile_kernels=1)
+    ctx = pp.pp_create(cfg, ox, oz, oc)
+    L = len(wl.circuit.layers)
+    for k, layer in enumerate(reversed(range(L))):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        before = pp.pp_stats(ctx)
+        if k == args.profile_layer:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+        pp.pp_apply_layer(ctx, pp.pack_gates(gx, gz), th, True)
+        if k == args.profile_layer:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            after = pp.pp_stats(ctx)
+            upd = after["gate_updates"] - before["gate_updates"]
+            ac = after["anticommuting_terms"] - before["anticommuting_terms"]
+            per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
+            print(json.dumps({"profile_layer": k, "updates": upd, "anticommuting_terms": ac,
+                              "algorithmic_bytes": KEY_BYTES * upd + per_ac * ac,
+                              "layer_kernel_ms": after["gate_kernel_ms"] - before["gate_kernel_ms"],
+                              "launches": after["gate_kernels_timed"] - before["gate_kernels_timed"],
+                              "live_terms": after["live_terms"]}), flush=True)
+    pp.pp_destroy(ctx)
+
+
 def bench_reference(args):
     """The oracle as the reference arm, on the host cores (rank 0 only)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -321,10 +358,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--profile-layer", type=int, default=-1,
+                    help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     ap.add_argument("--profile-timed", action="store_true",
                     help="also bracket every gate kernel with events inside the timed steps")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_layer >= 0:
+        profile_layer(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_ours(args)

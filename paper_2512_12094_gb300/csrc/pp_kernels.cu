@@ -80,21 +80,31 @@ __device__ __forceinline__ bool keys_equal(const Key<W>& a, const Key<W>& b) {
   return eq;
 }
 
-__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
-  h ^= h >> 33;
-  h *= 0xff51afd7ed558ccdull;
-  h ^= h >> 33;
-  h *= 0xc4ceb9fe1a85ec53ull;
-  h ^= h >> 33;
+// 64-bit hash of a key built from 32-bit multiplies only (murmur3-style
+// mixing of the 32-bit halves, two lanes with different constants).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
   return h;
 }
 
 template <int W>
 __device__ __forceinline__ uint64_t key_hash(const Key<W>& k) {
-  uint64_t h = 0x9E3779B97F4A7C15ull;
+  uint32_t a = 0x9E3779B9u, b = 0x7F4A7C15u;
 #pragma unroll
-  for (int j = 0; j < 2 * W; ++j) h = fmix64(h ^ k.w[j]);
-  return h;
+  for (int j = 0; j < 2 * W; ++j) {
+    const uint32_t lo = (uint32_t)k.w[j], hi = (uint32_t)(k.w[j] >> 32);
+    a = (a ^ lo) * 0xcc9e2d51u;
+    a = __funnelshift_l(a, a, 15) ^ hi;
+    a *= 0x1b873593u;
+    b = (b ^ hi) * 0x27d4eb2fu;
+    b = __funnelshift_l(b, b, 13) ^ lo;
+    b *= 0x165667b1u;
+  }
+  return ((uint64_t)fmix32(a ^ b) << 32) | fmix32(b + 0x9E3779B9u * a);
 }
 
 __device__ __forceinline__ uint32_t tag_of(uint64_t h) { return (uint32_t)(h >> 32) | 0x80000000u; }
