@@ -66,8 +66,12 @@ typedef struct {
 typedef struct {
   int n_qubits;            /* 1..256 */
   int symmetry;            /* pp_symmetry: group used by merges and overlaps */
-  int batch;               /* must be 1 (one angle set) */
-  int coef_type;           /* pp_coef_type; PP_COEF_F64 only */
+  int batch;               /* B = number of angle sets sharing the circuit, 1..512; every
+                              string then carries B coefficients and is kept iff some
+                              column satisfies the truncation rule */
+  int coef_type;           /* pp_coef_type: storage (and gate arithmetic) precision of the
+                              coefficients; merges accumulate and overlaps sum in FP64
+                              in both cases */
   double coeff_eps;        /* coefficient truncation threshold; 0 = off */
   int max_weight;          /* Pauli-weight truncation; < 0 = off */
   int noise_mode;          /* pp_noise_mode */
@@ -108,7 +112,7 @@ typedef struct {
 pp_status pp_config_default(pp_config* cfg);
 
 /* Create a context holding O = sum_i coef[i] s_i (Algorithm 1, step 1).
- * x, z: host arrays [n_terms][W]; coef: host array [n_terms].  Duplicate
+ * x, z: host arrays [n_terms][W]; coef: host array [n_terms][batch].  Duplicate
  * strings accumulate.  With cfg->symmetry != PP_SYM_NONE the strings are
  * mapped to their orbit representatives and merged, giving O~_L of Alg. 1.
  * The truncation rules are then applied.  n_terms may be 0.
@@ -127,12 +131,12 @@ pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t
 pp_status pp_destroy(pp_ctx* ctx);
 
 /* One Heisenberg layer O_{l-1} = U_l^dag O~_l U_l (Algorithm 1, step 2a, and
- * Appendix A).  gates[0..n_gates) and theta[0..n_gates) describe U_l in TIME
+ * Appendix A).  gates[0..n_gates) and theta[n_gates][batch] describe U_l in TIME
  * order; they are applied from the last to the first.  Per gate: per-gate
  * damping (noise_mode PER_GATE: c <- c (1-p)^k, k = non-identity sites of Q on
  * the gate's support), conjugation, merge of identical strings, truncation.
  * noise_mode PER_LAYER damps every term by exp(-p |Q|) once before the gates
- * (the noise layer follows U_l in time).  With symmetric_boundary != 0 the
+ * (the noise layer follows U_l in time; batch 1 with FP64 storage only).  With symmetric_boundary != 0 the
  * layer ends with the symmetry merge of Eq. (O-merging) (Algorithm 2 for
  * Z_n, Algorithm 3 for S_n) and another truncation.  Callers apply layers
  * from the last (l = L) to the first (l = 1).
@@ -165,7 +169,7 @@ pp_status pp_truncate(pp_ctx* ctx, double eps, int max_weight);
  * representative r contributes c_r times the orbit average of Tr[rho g.r],
  * which equals Tr[rho r] when rho is symmetric (Eq. 2) and keeps the result
  * exact for a symmetric O when rho is not.  The sum is accumulated in FP64
- * in a fixed order.  *out receives one double.
+ * in a fixed order.  out receives `batch` doubles (one per angle set).
  * Errors: PP_ERR_SYMMETRY when neither rho nor the ingested O is invariant. */
 pp_status pp_expect(pp_ctx* ctx, const double* bloch, double* out);
 
@@ -173,7 +177,7 @@ pp_status pp_expect(pp_ctx* ctx, const double* bloch, double* out);
 pp_status pp_num_terms(pp_ctx* ctx, int64_t* live, int64_t* stored);
 
 /* Copy the live terms to host arrays x, z [capacity][W] and coef
- * [capacity]; *n_out receives the count.  PP_ERR_ARG if capacity is too
+ * [capacity][batch] (FP64); *n_out receives the count.  PP_ERR_ARG if capacity is too
  * small (nothing written; *n_out still receives the count). */
 pp_status pp_export(pp_ctx* ctx, int64_t capacity, uint64_t* x, uint64_t* z, double* coef,
                     int64_t* n_out);

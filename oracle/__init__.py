@@ -71,6 +71,18 @@ def _load():
                                   u64p, u64p]
     lib.orc_sym_overlap.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, u64p, u64p,
                                     f64p, f64p]
+    lib.orcb_create.restype = P
+    lib.orcb_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, u64p, u64p, f64p,
+                                ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.orcb_destroy.argtypes = [P]
+    lib.orcb_size.restype = ctypes.c_longlong
+    lib.orcb_size.argtypes = [P]
+    lib.orcb_updates.restype = ctypes.c_double
+    lib.orcb_updates.argtypes = [P]
+    lib.orcb_apply_layer.argtypes = [P, ctypes.c_int, u64p, u64p, f64p, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.orcb_expect.argtypes = [P, f64p, ctypes.c_int, f64p]
+    lib.orcb_export.argtypes = [P, u64p, u64p, f64p]
     _lib = lib
     return lib
 
@@ -157,6 +169,60 @@ class OracleState:
         x, z, c = self.export()
         return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
                 for i in range(len(c))}
+
+
+class BatchedOracleState:
+    """B angle sets on one circuit: every string carries B coefficients; a
+    term is kept iff some column has |c| >= eps."""
+
+    def __init__(self, n, B, x, z, coef, group=0, eps=0.0, max_weight=-1):
+        lib = _load()
+        self.n, self.B, self.W = n, B, (n + 63) // 64
+        xa, xp = _u64(np.asarray(x).reshape(-1, self.W))
+        za, zp = _u64(np.asarray(z).reshape(-1, self.W))
+        ca, cp = _f64(np.asarray(coef, dtype=np.float64).reshape(-1, B))
+        self._h = lib.orcb_create(n, xa.shape[0], B, xp, zp, cp, group, eps, max_weight)
+        self.group, self.eps, self.max_weight = group, eps, max_weight
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orcb_destroy(h)
+            self._h = None
+
+    def __len__(self):
+        return int(_lib.orcb_size(self._h))
+
+    @property
+    def updates(self) -> float:
+        return float(_lib.orcb_updates(self._h))
+
+    def apply_layer(self, gx, gz, theta, noise_mode=0, p=0.0, group=None):
+        """theta: [K, B] angles (time order of the K gates)."""
+        g = self.group if group is None else group
+        ga, gp = _u64(gx)
+        ha, hp = _u64(gz)
+        ta, tp = _f64(np.asarray(theta, dtype=np.float64).reshape(-1, self.B))
+        _lib.orcb_apply_layer(self._h, ta.shape[0], gp, hp, tp, noise_mode, p, self.eps,
+                              self.max_weight, g)
+
+    def expect(self, bloch, group=None):
+        g = self.group if group is None else group
+        ba, bp = _f64(np.asarray(bloch).reshape(-1))
+        out = np.zeros(self.B)
+        _lib.orcb_expect(self._h, bp, g, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def export(self):
+        m = len(self)
+        x = np.zeros((m, self.W), dtype=np.uint64)
+        z = np.zeros((m, self.W), dtype=np.uint64)
+        c = np.zeros((m, self.B), dtype=np.float64)
+        if m:
+            _lib.orcb_export(self._h, x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                             z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return x, z, c
 
 
 def canonical(n: int, group: int, x, z):

@@ -403,3 +403,172 @@ void orc_sym_overlap(int n, long long m, int group, const uint64_t* x, const uin
 }
 
 }  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------------------
+// Batched angles: B angle sets share one circuit structure, so every string
+// carries a row of B coefficients.  A term is kept iff some column has
+// |c_b| >= eps (and its weight is allowed).  Each column follows exactly the
+// single-set rules above with its own angles.
+// ------------------------------------------------------------------------
+
+struct BState {
+  int n = 0, W = 1, B = 1;
+  std::unordered_map<std::string, std::vector<double>> terms;
+  double updates = 0.0;
+  State helper;  // for overlaps (S_n table cache)
+};
+
+bool keep_row(const std::vector<double>& c, const std::string& s, double eps, int wmax) {
+  if (wmax >= 0 && weight(s) > wmax) return false;
+  if (eps <= 0.0) return true;
+  for (double v : c)
+    if (std::fabs(v) >= eps) return true;
+  return false;
+}
+
+void btruncate(BState* st, double eps, int wmax) {
+  for (auto it = st->terms.begin(); it != st->terms.end();) {
+    if (!keep_row(it->second, it->first, eps, wmax))
+      it = st->terms.erase(it);
+    else
+      ++it;
+  }
+}
+
+void bmerge(BState* st, int group) {
+  std::unordered_map<std::string, std::vector<double>> merged;
+  for (const auto& kv : st->terms) {
+    auto& row = merged[canonical(kv.first, group)];
+    if (row.empty()) row.assign(st->B, 0.0);
+    for (int b = 0; b < st->B; ++b) row[b] += kv.second[b];
+  }
+  st->terms.swap(merged);
+}
+
+void bapply_gate(BState* st, const std::string& P, const double* theta, int noise_mode, double p,
+                 double eps, int wmax) {
+  const int B = st->B;
+  std::vector<double> c(B), s(B);
+  for (int b = 0; b < B; ++b) {
+    c[b] = std::cos(theta[b]);
+    s[b] = std::sin(theta[b]);
+  }
+  std::vector<int> support;
+  for (int q = 0; q < st->n; ++q)
+    if (P[q] != 0) support.push_back(q);
+  std::vector<double> damp(support.size() + 1, 1.0);
+  for (size_t k = 1; k < damp.size(); ++k) damp[k] = damp[k - 1] * (1.0 - p);
+  st->updates += (double)st->terms.size();
+  std::unordered_map<std::string, std::vector<double>> next;
+  auto row_of = [&](const std::string& key) -> std::vector<double>& {
+    auto& r = next[key];
+    if (r.empty()) r.assign(B, 0.0);
+    return r;
+  };
+  for (const auto& kv : st->terms) {
+    const std::string& Q = kv.first;
+    std::vector<double> d = kv.second;
+    if (noise_mode == 1) {
+      int k = 0;
+      for (int q : support) k += (Q[q] != 0);
+      if (k > 0)
+        for (int b = 0; b < B; ++b) d[b] = d[b] * damp[k];
+    }
+    int anti = 0;
+    for (int q : support) anti += site_anticommutes((uint8_t)P[q], (uint8_t)Q[q]);
+    if (anti % 2 == 0) {
+      auto& r = row_of(Q);
+      for (int b = 0; b < B; ++b) r[b] += d[b];
+      continue;
+    }
+    std::string R = Q;
+    int phase = 0;
+    for (int q : support) {
+      const Prod& pr = kMul[(uint8_t)P[q]][(uint8_t)Q[q]];
+      R[q] = (char)pr.letter;
+      phase += pr.phase;
+    }
+    double sign = ((phase + 1) % 4 == 0) ? 1.0 : -1.0;
+    auto& rq = row_of(Q);
+    for (int b = 0; b < B; ++b) rq[b] += c[b] * d[b];
+    auto& rr = row_of(R);
+    for (int b = 0; b < B; ++b) rr[b] += sign * (s[b] * d[b]);
+  }
+  st->terms.swap(next);
+  btruncate(st, eps, wmax);
+}
+
+}  // namespace
+
+extern "C" {
+
+void* orcb_create(int n, long long n_terms, int B, const uint64_t* x, const uint64_t* z,
+                  const double* coef, int group, double eps, int wmax) {
+  BState* st = new BState();
+  st->n = n;
+  st->W = (n + 63) / 64;
+  st->B = B;
+  st->helper.n = n;
+  st->helper.W = st->W;
+  for (long long i = 0; i < n_terms; ++i) {
+    std::string s = letters_from_masks(n, st->W, x + i * st->W, z + i * st->W);
+    auto& r = st->terms[s];
+    if (r.empty()) r.assign(B, 0.0);
+    for (int b = 0; b < B; ++b) r[b] += coef[i * B + b];
+  }
+  if (group != 0) bmerge(st, group);
+  btruncate(st, eps, wmax);
+  return st;
+}
+
+void orcb_destroy(void* h) { delete (BState*)h; }
+long long orcb_size(void* h) { return (long long)((BState*)h)->terms.size(); }
+double orcb_updates(void* h) { return ((BState*)h)->updates; }
+
+// Layer in time order, theta = [n_gates][B]; applied last gate first, then
+// the symmetry merge when group != 0.
+int orcb_apply_layer(void* h, int n_gates, const uint64_t* gx, const uint64_t* gz,
+                     const double* theta, int noise_mode, double p, double eps, int wmax,
+                     int group) {
+  BState* st = (BState*)h;
+  for (int g = n_gates - 1; g >= 0; --g) {
+    std::string P = letters_from_masks(st->n, st->W, gx + (size_t)g * st->W, gz + (size_t)g * st->W);
+    bapply_gate(st, P, theta + (size_t)g * st->B, noise_mode, p, eps, wmax);
+  }
+  if (group != 0) {
+    bmerge(st, group);
+    btruncate(st, eps, wmax);
+  }
+  return 0;
+}
+
+void orcb_expect(void* h, const double* bloch, int group, double* out) {
+  BState* st = (BState*)h;
+  for (int b = 0; b < st->B; ++b) out[b] = 0.0;
+  for (const auto& kv : st->terms) {
+    double ov = sym_overlap(&st->helper, kv.first, bloch, group);
+    for (int b = 0; b < st->B; ++b) out[b] += kv.second[b] * ov;
+  }
+}
+
+void orcb_export(void* h, uint64_t* x, uint64_t* z, double* coef) {
+  BState* st = (BState*)h;
+  std::vector<std::pair<std::vector<uint64_t>, const std::vector<double>*>> rows;
+  for (const auto& kv : st->terms) {
+    std::vector<uint64_t> key(2 * st->W);
+    masks_from_letters(kv.first, st->W, key.data(), key.data() + st->W);
+    rows.emplace_back(std::move(key), &kv.second);
+  }
+  std::sort(rows.begin(), rows.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  for (size_t i = 0; i < rows.size(); ++i) {
+    for (int w = 0; w < st->W; ++w) {
+      x[i * st->W + w] = rows[i].first[w];
+      z[i * st->W + w] = rows[i].first[st->W + w];
+    }
+    for (int b = 0; b < st->B; ++b) coef[i * st->B + b] = (*rows[i].second)[b];
+  }
+}
+
+}  // extern "C"

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _LIB = os.path.join(_HERE, "libpp.so")
-_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu"]
+_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu", "pp_batched.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -49,7 +49,8 @@ def _nvcc():
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libpp.so in-tree for sm_103a (objects in parallel, then link)."""
     srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
-    deps = srcs + [os.path.join(_CSRC, "pp_internal.h"), os.path.join(_ROOT, "include", "pp.h")]
+    deps = srcs + [os.path.join(_CSRC, "pp_internal.h"), os.path.join(_CSRC, "pp_device.cuh"),
+                   os.path.join(_ROOT, "include", "pp.h")]
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(d) for d in deps)):
         return _LIB
@@ -181,13 +182,14 @@ def pp_config_default(**kw) -> pp_config:
 
 
 def pp_create(cfg: pp_config, x, z, coef):
-    """x, z: uint64 [m, W] host arrays; coef: float64 [m]."""
+    """x, z: uint64 [m, W] host arrays; coef: float64 [m] or [m, batch]."""
     W = (cfg.n_qubits + 63) // 64
     x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64).reshape(-1, W))
     z = np.ascontiguousarray(np.asarray(z, dtype=np.uint64).reshape(-1, W))
-    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, cfg.batch))
     h = _vp()
-    _check(load().pp_create(ctypes.byref(cfg), len(c), _ptr(x), _ptr(z), _ptr(c), ctypes.byref(h)))
+    _check(load().pp_create(ctypes.byref(cfg), c.shape[0], _ptr(x), _ptr(z), _ptr(c),
+                            ctypes.byref(h)))
     return h
 
 
@@ -215,10 +217,10 @@ def pack_gates(gx, gz) -> np.ndarray:
 
 
 def pp_apply_layer(ctx, gates_packed: np.ndarray, theta, symmetric_boundary: bool):
-    """gates_packed from pack_gates (time order); theta float64 [K]."""
-    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    """gates_packed from pack_gates (time order); theta float64 [K] or [K, batch]."""
     g = np.ascontiguousarray(gates_packed)
-    _check(load().pp_apply_layer(ctx, len(th), _ptr(g), _ptr(th), int(bool(symmetric_boundary))))
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    _check(load().pp_apply_layer(ctx, g.shape[0], _ptr(g), _ptr(th), int(bool(symmetric_boundary))))
 
 
 def pp_canonicalize(ctx):
@@ -233,11 +235,12 @@ def pp_truncate(ctx, eps: float, max_weight: int):
     _check(load().pp_truncate(ctx, float(eps), int(max_weight)))
 
 
-def pp_expect(ctx, bloch) -> float:
+def pp_expect(ctx, bloch, batch: int = 1):
+    """Tr[rho O]: a float, or float64 [batch] for a batched context."""
     b = np.ascontiguousarray(np.asarray(bloch, dtype=np.float64).reshape(-1))
-    out = ctypes.c_double()
-    _check(load().pp_expect(ctx, _ptr(b), ctypes.byref(out)))
-    return out.value
+    out = np.zeros(batch, dtype=np.float64)
+    _check(load().pp_expect(ctx, _ptr(b), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return float(out[0]) if batch == 1 else out
 
 
 def pp_num_terms(ctx):
@@ -246,7 +249,8 @@ def pp_num_terms(ctx):
     return live.value, stored.value
 
 
-def pp_export(ctx, n_qubits: int):
+def pp_export(ctx, n_qubits: int, batch: int = 1):
+    """(x [m, W], z [m, W], coef [m] or [m, batch]) of the live terms."""
     W = (n_qubits + 63) // 64
     m = ctypes.c_int64()
     st = load().pp_export(ctx, 0, None, None, None, ctypes.byref(m))
@@ -255,7 +259,7 @@ def pp_export(ctx, n_qubits: int):
     cap = m.value
     x = np.zeros((cap, W), dtype=np.uint64)
     z = np.zeros((cap, W), dtype=np.uint64)
-    c = np.zeros(cap, dtype=np.float64)
+    c = np.zeros((cap, batch) if batch > 1 else cap, dtype=np.float64)
     _check(load().pp_export(ctx, cap, _ptr(x), _ptr(z), _ptr(c), ctypes.byref(m)))
     return x[:m.value], z[:m.value], c[:m.value]
 
@@ -320,7 +324,7 @@ class Propagator:
 
     def __init__(self, n_qubits, x, z, coef, symmetry=SYM_NONE, eps=0.0, max_weight=-1,
                  noise_mode=NOISE_NONE, noise_p=0.0, budget=0, stream=None, use_graphs=True,
-                 check_symmetry=True, profile=False, layer_kernel=True):
+                 check_symmetry=True, profile=False, layer_kernel=True, batch=1, f32=False):
         self.n = n_qubits
         self.cfg = pp_config_default(n_qubits=n_qubits, symmetry=symmetry, coeff_eps=eps,
                                      max_weight=max_weight, noise_mode=noise_mode,
@@ -328,7 +332,9 @@ class Propagator:
                                      cuda_stream=stream, use_graphs=int(use_graphs),
                                      check_symmetry=int(check_symmetry),
                                      profile_kernels=int(profile),
-                                     layer_kernel=int(layer_kernel))
+                                     layer_kernel=int(layer_kernel), batch=int(batch),
+                                     coef_type=1 if f32 else 0)
+        self.batch = int(batch)
         self.ctx = pp_create(self.cfg, x, z, coef)
         self._packed = {}
 
@@ -371,14 +377,14 @@ class Propagator:
             return vals
         return self.expect(wl.state.bloch)
 
-    def expect(self, bloch) -> float:
-        return pp_expect(self.ctx, bloch)
+    def expect(self, bloch):
+        return pp_expect(self.ctx, bloch, self.batch)
 
     def num_terms(self):
         return pp_num_terms(self.ctx)
 
     def export(self):
-        return pp_export(self.ctx, self.n)
+        return pp_export(self.ctx, self.n, self.batch)
 
     def stats(self):
         return pp_stats(self.ctx)

@@ -65,7 +65,9 @@ int popcount64(uint64_t v) { return __builtin_popcountll(v); }
 
 struct Buf {
   uint64_t* keys = nullptr;
-  double* coef = nullptr;
+  double* coef = nullptr;           // single FP64 column
+  void* rows = nullptr;             // batched rows [cap][B]
+  unsigned char* alive = nullptr;   // batched liveness
   uint64_t* index = nullptr;
   uint64_t cap = 0;
   uint64_t icap = 0;
@@ -85,8 +87,10 @@ struct GraphEntry {
   uint64_t last_use = 0;
 };
 
-size_t table_bytes(uint64_t cap, uint64_t icap, int W) {
-  return (size_t)cap * (16 * W + 8) + (size_t)icap * 8;
+// row_bytes: coefficient bytes per string (8, or B x element size + 1 for the
+// liveness byte of batched rows)
+size_t table_bytes(uint64_t cap, uint64_t icap, int W, size_t row_bytes) {
+  return (size_t)cap * (16 * W + row_bytes) + (size_t)icap * 8;
 }
 
 }  // namespace
@@ -94,6 +98,12 @@ size_t table_bytes(uint64_t cap, uint64_t icap, int W) {
 struct pp_ctx {
   pp_config cfg{};
   int n = 0, W = 1;
+  int B = 1;             // angle sets (columns)
+  bool batched = false;  // rows + liveness bytes instead of one FP64 column
+  int f32 = 0;           // batched rows hold float
+  size_t esize = 8;      // bytes per row element
+  size_t row_bytes() const { return batched ? (size_t)B * esize + 1 : 8; }
+  std::vector<ArgsEntry> cs_cache;  // per-gate cos/sin columns (batched)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int sms = 1;
@@ -155,7 +165,12 @@ pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
   b.cap = cap;
   b.icap = index_cap_for(cap);
   PP_TRY(dmalloc(c, (void**)&b.keys, (size_t)cap * 16 * c->W));
-  PP_TRY(dmalloc(c, (void**)&b.coef, (size_t)cap * 8));
+  if (c->batched) {
+    PP_TRY(dmalloc(c, (void**)&b.rows, (size_t)cap * c->B * c->esize));
+    PP_TRY(dmalloc(c, (void**)&b.alive, (size_t)cap));
+  } else {
+    PP_TRY(dmalloc(c, (void**)&b.coef, (size_t)cap * 8));
+  }
   PP_TRY(dmalloc(c, (void**)&b.index, (size_t)b.icap * 8));
   PP_CUDA(cudaMemsetAsync(b.index, 0, (size_t)b.icap * 8, c->stream));
   return PP_OK;
@@ -164,24 +179,30 @@ pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
 void free_buf(pp_ctx* c, Buf& b) {
   dfree(c, b.keys, (size_t)b.cap * 16 * c->W);
   dfree(c, b.coef, (size_t)b.cap * 8);
+  dfree(c, b.rows, (size_t)b.cap * c->B * c->esize);
+  dfree(c, b.alive, (size_t)b.cap);
   dfree(c, b.index, (size_t)b.icap * 8);
   b = Buf();
 }
 
-DevTable desc_of(const Buf& b) {
+DevTable desc_of(const pp_ctx* c, const Buf& b) {
   DevTable t;
   t.keys = b.keys;
   t.coef = b.coef;
   t.index = b.index;
   t.cap = b.cap;
   t.imask = b.icap - 1;
+  t.rows = b.rows;
+  t.alive = b.alive;
+  t.B = c->B;
+  t.f32 = c->f32;
   return t;
 }
 
 // Write the descriptors of both tables and the active copy (synchronous
 // copy from host memory; only called when a table is (re)allocated).
 pp_status publish_desc(pp_ctx* c) {
-  DevTable h[3] = {desc_of(c->buf[0]), desc_of(c->buf[1]), desc_of(c->buf[c->active])};
+  DevTable h[3] = {desc_of(c, c->buf[0]), desc_of(c, c->buf[1]), desc_of(c, c->buf[c->active])};
   PP_CUDA(cudaStreamSynchronize(c->stream));
   PP_CUDA(cudaMemcpy(c->d_desc, h, sizeof(h), cudaMemcpyHostToDevice));
   return PP_OK;
@@ -245,9 +266,15 @@ pp_status compact_into(pp_ctx* c, int dst, double extra_eps, int extra_wmax) {
   Buf& d = c->buf[dst];
   PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
   PP_TRY(ctl_prepare_insert(c, 0));
-  PP_CUDA(launch_compact(c->W, grid_for(c, c->n_terms, 4), c->stream, desc_of(c->buf[c->active]),
-                         c->n_terms, desc_of(d), 1, c->cfg.coeff_eps, extra_eps, extra_wmax,
-                         c->d_ctl));
+  if (c->batched) {
+    PP_CUDA(launch_compact_batched(c->W, grid_for(c, c->n_terms, 4), c->stream,
+                                   desc_of(c, c->buf[c->active]), c->n_terms, desc_of(c, d), 1,
+                                   extra_eps, extra_wmax, c->d_ctl));
+  } else {
+    PP_CUDA(launch_compact(c->W, grid_for(c, c->n_terms, 4), c->stream,
+                           desc_of(c, c->buf[c->active]), c->n_terms, desc_of(c, d), 1,
+                           c->cfg.coeff_eps, extra_eps, extra_wmax, c->d_ctl));
+  }
   c->launches += 1;
   PP_TRY(ctl_commit(c));
   PP_TRY(activate(c, dst));
@@ -259,8 +286,8 @@ pp_status ensure_capacity(pp_ctx* c, uint64_t need) {
   if (need <= c->buf[c->active].cap) return PP_OK;
   uint64_t cap = std::max<uint64_t>(need, 1024);
   cap = (cap + 1023) & ~1023ull;
-  size_t add = 2 * table_bytes(cap, index_cap_for(cap), c->W);
-  size_t keep = c->bytes - 2 * table_bytes(c->buf[0].cap, c->buf[0].icap, c->W);
+  size_t add = 2 * table_bytes(cap, index_cap_for(cap), c->W, c->row_bytes());
+  size_t keep = c->bytes - 2 * table_bytes(c->buf[0].cap, c->buf[0].icap, c->W, c->row_bytes());
   if (c->cfg.mem_budget_bytes && keep + add > c->cfg.mem_budget_bytes)
     return fail(PP_ERR_CAPACITY, "term table of capacity " + std::to_string(cap) +
                                      " exceeds the memory budget");
@@ -298,11 +325,25 @@ pp_status merge_active(pp_ctx* c, int group) {
   Buf& s = c->buf[c->active];
   PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
   PP_TRY(ctl_prepare_insert(c, 0));
-  PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid_for(c, c->n_terms, 4), c->stream,
-                              s.keys, s.coef, c->n_terms, nullptr, c->cfg.coeff_eps > 0.0 ? 1 : 0,
-                              desc_of(d), c->d_ctl));
-  PP_CUDA(launch_finalize(grid_for(c, c->n_terms, 4), c->stream, desc_of(d), c->d_ctl,
-                          c->cfg.coeff_eps));
+  if (c->batched) {
+    // FP64 accumulation rows, rounded to the storage type by the finalize pass
+    double* acc = nullptr;
+    const size_t acc_bytes = (size_t)std::max<uint64_t>(c->n_terms, 1) * c->B * sizeof(double);
+    PP_TRY(dmalloc(c, (void**)&acc, acc_bytes));
+    PP_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, c->stream));
+    PP_CUDA(launch_merge_batched(c->W, group, c->n, -1, c->f32, grid_for(c, c->n_terms, 32),
+                                 c->stream, s.keys, s.rows, s.alive, c->n_terms, desc_of(c, d), acc,
+                                 c->d_ctl));
+    PP_CUDA(launch_finalize_batched(grid_for(c, c->n_terms, 32), c->stream, desc_of(c, d), acc,
+                                    c->d_ctl, c->cfg.coeff_eps));
+    dfree(c, acc, acc_bytes);
+  } else {
+    PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid_for(c, c->n_terms, 4), c->stream,
+                                s.keys, s.coef, c->n_terms, nullptr,
+                                c->cfg.coeff_eps > 0.0 ? 1 : 0, desc_of(c, d), c->d_ctl));
+    PP_CUDA(launch_finalize(grid_for(c, c->n_terms, 4), c->stream, desc_of(c, d), c->d_ctl,
+                            c->cfg.coeff_eps));
+  }
   c->launches += 2;
   PP_TRY(ctl_commit(c));
   PP_TRY(activate(c, dst));
@@ -396,8 +437,11 @@ pp_status validate_config(const pp_config* cfg) {
     return fail(PP_ERR_ARG, "n_qubits must be in 1..256");
   if (cfg->symmetry < PP_SYM_NONE || cfg->symmetry > PP_SYM_SN)
     return fail(PP_ERR_ARG, "unknown symmetry");
-  if (cfg->batch != 1) return fail(PP_ERR_ARG, "batch must be 1");
-  if (cfg->coef_type != PP_COEF_F64) return fail(PP_ERR_ARG, "only PP_COEF_F64 is supported");
+  if (cfg->batch < 1 || cfg->batch > 512) return fail(PP_ERR_ARG, "batch must be in 1..512");
+  if (cfg->coef_type != PP_COEF_F64 && cfg->coef_type != PP_COEF_F32)
+    return fail(PP_ERR_ARG, "unknown coef_type");
+  if ((cfg->batch > 1 || cfg->coef_type == PP_COEF_F32) && cfg->noise_mode == PP_NOISE_PER_LAYER)
+    return fail(PP_ERR_ARG, "per-layer noise needs batch 1 and FP64 storage");
   if (!(cfg->coeff_eps >= 0.0)) return fail(PP_ERR_ARG, "coeff_eps must be >= 0");
   if (cfg->noise_mode < PP_NOISE_NONE || cfg->noise_mode > PP_NOISE_PER_LAYER)
     return fail(PP_ERR_ARG, "unknown noise mode");
@@ -418,6 +462,10 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   c->cfg = *cfg;
   c->n = cfg->n_qubits;
   c->W = (c->n + 63) / 64;
+  c->B = cfg->batch;
+  c->batched = cfg->batch > 1 || cfg->coef_type == PP_COEF_F32;
+  c->f32 = cfg->coef_type == PP_COEF_F32 ? 1 : 0;
+  c->esize = c->f32 ? 4 : 8;
   c->sms = std::max(1, device_sm_count());
   c->gate_bps = gate_blocks_per_sm(c->W);
 
@@ -446,12 +494,12 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   if ((st = dmalloc(c, (void**)&c->d_desc, 3 * sizeof(DevTable))) != PP_OK) return cleanup(st);
   if ((st = dmalloc(c, (void**)&c->d_ctl, sizeof(DevCtl))) != PP_OK) return cleanup(st);
   if (cudaMallocHost((void**)&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->h_out, sizeof(double)) != cudaSuccess)
+      cudaMallocHost((void**)&c->h_out, sizeof(double) * cfg->batch) != cudaSuccess)
     return cleanup(fail(PP_ERR_OOM, "pinned host allocation failed"));
   memset(c->h_ctl, 0, sizeof(DevCtl));
   c->overlap_grid = c->sms * 4;
-  if ((st = dmalloc(c, (void**)&c->d_partials, sizeof(double) * c->overlap_grid)) != PP_OK ||
-      (st = dmalloc(c, (void**)&c->d_out, sizeof(double))) != PP_OK ||
+  if ((st = dmalloc(c, (void**)&c->d_partials, sizeof(double) * c->overlap_grid * c->B)) != PP_OK ||
+      (st = dmalloc(c, (void**)&c->d_out, sizeof(double) * c->B)) != PP_OK ||
       (st = dmalloc(c, (void**)&c->d_bloch, sizeof(double) * 3 * c->n)) != PP_OK ||
       (st = dmalloc(c, (void**)&c->d_damp, sizeof(double) * (c->n + 1))) != PP_OK ||
       (st = dmalloc(c, (void**)&c->d_ldamp, sizeof(double) * (c->n + 1))) != PP_OK)
@@ -471,7 +519,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   }
   uint64_t cap = std::max<uint64_t>(4 * (uint64_t)n_terms, 1024);
   cap = (cap + 1023) & ~1023ull;
-  size_t need = 2 * table_bytes(cap, index_cap_for(cap), W) + c->bytes;
+  size_t need = 2 * table_bytes(cap, index_cap_for(cap), W, c->row_bytes()) + c->bytes;
   if (cfg->mem_budget_bytes && need > cfg->mem_budget_bytes)
     return cleanup(fail(PP_ERR_CAPACITY, "initial table exceeds the memory budget"));
   if ((st = alloc_buf(c, c->buf[0], cap)) != PP_OK || (st = alloc_buf(c, c->buf[1], cap)) != PP_OK)
@@ -485,7 +533,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   if (n_terms > 0) {
     hx.resize((size_t)n_terms * W);
     hz.resize((size_t)n_terms * W);
-    hc.resize((size_t)n_terms);
+    hc.resize((size_t)n_terms * c->B);
     if (on_device) {
       if (cudaMemcpyAsync(hx.data(), x, hx.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
           cudaMemcpyAsync(hz.data(), z, hz.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -502,22 +550,26 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
         return cleanup(fail(PP_ERR_ARG, "a string has bits at or above n_qubits"));
   }
   if (cfg->symmetry != PP_SYM_NONE) {
-    std::map<HKey, double> acc;
-    for (int64_t i = 0; i < n_terms; ++i) {
-      HKey k(2 * W);
-      for (int j = 0; j < W; ++j) {
-        k[j] = hx[i * W + j];
-        k[W + j] = hz[i * W + j];
+    // the observable is invariant when every column is
+    c->obs_invariant = true;
+    for (int b = 0; b < c->B && c->obs_invariant; ++b) {
+      std::map<HKey, double> acc;
+      for (int64_t i = 0; i < n_terms; ++i) {
+        HKey k(2 * W);
+        for (int j = 0; j < W; ++j) {
+          k[j] = hx[i * W + j];
+          k[W + j] = hz[i * W + j];
+        }
+        acc[k] += hc[(size_t)i * c->B + b];
       }
-      acc[k] += hc[i];
+      std::vector<HKey> ks;
+      std::vector<double> vs;
+      for (auto& kv : acc) {
+        ks.push_back(kv.first);
+        vs.push_back(kv.second);
+      }
+      c->obs_invariant = multiset_invariant(cfg->symmetry, c->n, W, ks, vs, 1e-12);
     }
-    std::vector<HKey> ks;
-    std::vector<double> vs;
-    for (auto& kv : acc) {
-      ks.push_back(kv.first);
-      vs.push_back(kv.second);
-    }
-    c->obs_invariant = multiset_invariant(cfg->symmetry, c->n, W, ks, vs, 1e-12);
   }
 
   // Ingest: pack, then accumulate (with representatives when a group is set).
@@ -526,7 +578,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
     double* d_coef = nullptr;
     unsigned* d_bad = nullptr;
     if ((st = dmalloc(c, (void**)&d_keys, (size_t)n_terms * 16 * W)) != PP_OK ||
-        (st = dmalloc(c, (void**)&d_coef, (size_t)n_terms * 8)) != PP_OK)
+        (st = dmalloc(c, (void**)&d_coef, hc.size() * 8)) != PP_OK)
       return cleanup(st);
     std::vector<uint64_t> packed((size_t)n_terms * 2 * W);
     for (int64_t i = 0; i < n_terms; ++i)
@@ -541,33 +593,54 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
             cudaSuccess)
       return cleanup(fail(PP_ERR_CUDA, "term upload failed"));
     if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return cleanup(st);
-    cudaError_t e = launch_merge_insert(W, cfg->symmetry, c->n, cfg->max_weight,
-                                        grid_for(c, n_terms, 4), c->stream, d_keys, d_coef,
-                                        (uint64_t)n_terms, nullptr, 0, desc_of(c->buf[0]), c->d_ctl);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "merge_insert"));
-    e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c->buf[0]), c->d_ctl,
-                        cfg->coeff_eps);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "finalize"));
-    if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
+    cudaError_t e;
+    if (c->batched) {
+      double* acc = nullptr;
+      const size_t acc_bytes = (size_t)n_terms * c->B * sizeof(double);
+      if ((st = dmalloc(c, (void**)&acc, acc_bytes)) != PP_OK) return cleanup(st);
+      e = cudaMemsetAsync(acc, 0, acc_bytes, c->stream);
+      if (e == cudaSuccess)
+        e = launch_merge_batched(W, cfg->symmetry, c->n, cfg->max_weight, 0,
+                                 grid_for(c, n_terms, 32), c->stream, d_keys, d_coef, nullptr,
+                                 (uint64_t)n_terms, desc_of(c, c->buf[0]), acc, c->d_ctl);
+      if (e == cudaSuccess)
+        e = launch_finalize_batched(grid_for(c, n_terms, 32), c->stream, desc_of(c, c->buf[0]),
+                                    acc, c->d_ctl, cfg->coeff_eps);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "batched ingest"));
+      if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
+      dfree(c, acc, acc_bytes);
+    } else {
+      e = launch_merge_insert(W, cfg->symmetry, c->n, cfg->max_weight, grid_for(c, n_terms, 4),
+                              c->stream, d_keys, d_coef, (uint64_t)n_terms, nullptr, 0,
+                              desc_of(c, c->buf[0]), c->d_ctl);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "merge_insert"));
+      e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c, c->buf[0]), c->d_ctl,
+                          cfg->coeff_eps);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "finalize"));
+      if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
+    }
     dfree(c, d_keys, (size_t)n_terms * 16 * W);
-    dfree(c, d_coef, (size_t)n_terms * 8);
+    dfree(c, d_coef, hc.size() * 8);
   }
   *out = c;
   return PP_OK;
 }
 
 // Build the gate arguments of one layer in application (reversed) order.
+// theta is [n_gates][B]; src receives the time index of every argument.
 pp_status build_gates(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
-                      std::vector<GateArgs>& out) {
+                      std::vector<GateArgs>& out, std::vector<int>& src) {
   const int W = c->W;
   out.clear();
+  src.clear();
   for (int t = n_gates - 1; t >= 0; --t) {
     const pp_pauli& P = gates[t];
     for (int j = W; j < kMaxW; ++j)
       if (P.x[j] || P.z[j]) return fail(PP_ERR_ARG, "gate has bits in unused words");
     if (key_has_bits_beyond(P.x, P.z, c->n, W))
       return fail(PP_ERR_ARG, "gate has bits at or above n_qubits");
-    if (!std::isfinite(theta[t])) return fail(PP_ERR_ARG, "non-finite angle");
+    for (int b = 0; b < c->B; ++b)
+      if (!std::isfinite(theta[(size_t)t * c->B + b])) return fail(PP_ERR_ARG, "non-finite angle");
     GateArgs g;
     memset(&g, 0, sizeof(g));
     int pyy = 0, pivot = -1;
@@ -586,8 +659,8 @@ pp_status build_gates(pp_ctx* c, int n_gates, const pp_pauli* gates, const doubl
       }
     }
     if (pivot < 0) continue;  // identity generator: a global phase, nothing to do
-    g.cth = std::cos(theta[t]);
-    g.sth = std::sin(theta[t]);
+    g.cth = std::cos(theta[(size_t)t * c->B]);
+    g.sth = std::sin(theta[(size_t)t * c->B]);
     g.damp = (c->cfg.noise_mode == PP_NOISE_PER_GATE) ? c->d_damp : nullptr;
     g.eps = c->cfg.coeff_eps;
     g.use_eps = c->cfg.coeff_eps > 0.0 ? 1 : 0;
@@ -600,7 +673,67 @@ pp_status build_gates(pp_ctx* c, int n_gates, const pp_pauli* gates, const doubl
       g.pvz[pivot - W] = pmask;
     g.gate_id = (unsigned)out.size();
     out.push_back(g);
+    src.push_back(t);
   }
+  return PP_OK;
+}
+
+// Device copy of a byte block, cached by content (gate arguments, per-gate
+// cos/sin columns).
+pp_status cached_upload(pp_ctx* c, std::vector<ArgsEntry>& cache,
+                        std::vector<unsigned char>&& bytes, const void** out) {
+  c->graph_clock++;
+  for (auto& e : cache) {
+    if (e.sig == bytes) {
+      e.last_use = c->graph_clock;
+      *out = e.d_args;
+      return PP_OK;
+    }
+  }
+  if (cache.size() >= 16) {
+    auto it = std::min_element(cache.begin(), cache.end(), [](const ArgsEntry& a, const ArgsEntry& b) {
+      return a.last_use < b.last_use;
+    });
+    dfree(c, it->d_args, it->n);
+    cache.erase(it);
+  }
+  ArgsEntry ent;
+  ent.n = bytes.size();
+  PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n));
+  PP_CUDA(cudaStreamSynchronize(c->stream));
+  PP_CUDA(cudaMemcpy(ent.d_args, bytes.data(), ent.n, cudaMemcpyHostToDevice));
+  ent.sig = std::move(bytes);
+  ent.last_use = c->graph_clock;
+  *out = ent.d_args;
+  cache.push_back(std::move(ent));
+  return PP_OK;
+}
+
+// Batched: cos and sin of every column of every gate, in the row element
+// type, and the pointer of each gate's block in its arguments.
+pp_status batched_columns(pp_ctx* c, std::vector<GateArgs>& args, const std::vector<int>& src,
+                          const double* theta) {
+  const int B = c->B;
+  std::vector<unsigned char> bytes(args.size() * 2 * B * c->esize);
+  for (size_t k = 0; k < args.size(); ++k) {
+    const double* th = theta + (size_t)src[k] * B;
+    for (int b = 0; b < B; ++b) {
+      const double cv = std::cos(th[b]), sv = std::sin(th[b]);
+      if (c->f32) {
+        float* f = reinterpret_cast<float*>(bytes.data()) + k * 2 * B;
+        f[b] = (float)cv;
+        f[B + b] = (float)sv;
+      } else {
+        double* d = reinterpret_cast<double*>(bytes.data()) + k * 2 * B;
+        d[b] = cv;
+        d[B + b] = sv;
+      }
+    }
+  }
+  const void* dev = nullptr;
+  PP_TRY(cached_upload(c, c->cs_cache, std::move(bytes), &dev));
+  for (size_t k = 0; k < args.size(); ++k)
+    args[k].csb = static_cast<const unsigned char*>(dev) + k * 2 * B * c->esize;
   return PP_OK;
 }
 
@@ -626,8 +759,9 @@ cudaError_t enqueue_gates(pp_ctx* c, const std::vector<GateArgs>& args, int grid
     cudaError_t e;
     if (prof && (e = cudaEventRecordWithFlags(c->ev_start[k], c->stream, flags)) != cudaSuccess)
       return e;
-    if ((e = launch_gate(c->W, grid, c->stream, tab, c->d_ctl, args[k], k > 0)) != cudaSuccess)
-      return e;
+    e = c->batched ? launch_gate_batched(c->W, c->f32, grid, c->stream, tab, c->d_ctl, args[k], k > 0)
+                   : launch_gate(c->W, grid, c->stream, tab, c->d_ctl, args[k], k > 0);
+    if (e != cudaSuccess) return e;
     if (prof && (e = cudaEventRecordWithFlags(c->ev_end[k], c->stream, flags)) != cudaSuccess)
       return e;
   }
@@ -780,8 +914,10 @@ pp_status pp_destroy(pp_ctx* c) {
   dfree(c, c->d_ctl, sizeof(DevCtl));
   dfree(c, c->d_damp, sizeof(double) * (c->n + 1));
   dfree(c, c->d_ldamp, sizeof(double) * (c->n + 1));
-  dfree(c, c->d_partials, sizeof(double) * c->overlap_grid);
-  dfree(c, c->d_out, sizeof(double));
+  dfree(c, c->d_partials, sizeof(double) * c->overlap_grid * c->B);
+  dfree(c, c->d_out, sizeof(double) * c->B);
+  for (auto& a : c->cs_cache) dfree(c, a.d_args, a.n);
+  c->cs_cache.clear();
   dfree(c, c->d_bloch, sizeof(double) * 3 * c->n);
   size_t sn = (size_t)(c->n + 1) * (c->n + 1) * (c->n + 1) * sizeof(double);
   dfree(c, c->d_sn, sn);
@@ -800,10 +936,10 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
   if (n_gates < 0 || (n_gates > 0 && (!gates || !theta)))
     return fail(PP_ERR_ARG, "bad gate arrays");
   std::vector<GateArgs> args;
-  PP_TRY(build_gates(c, n_gates, gates, theta, args));
+  std::vector<int> src_t;
+  PP_TRY(build_gates(c, n_gates, gates, theta, args, src_t));
   if (c->cfg.symmetry != PP_SYM_NONE && c->cfg.check_symmetry && n_gates > 0) {
     std::vector<HKey> ks;
-    std::vector<double> vs;
     for (int t = 0; t < n_gates; ++t) {
       HKey k(2 * c->W);
       for (int j = 0; j < c->W; ++j) {
@@ -811,20 +947,24 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
         k[c->W + j] = gates[t].z[j];
       }
       ks.push_back(k);
-      vs.push_back(theta[t]);
     }
-    if (!multiset_invariant(c->cfg.symmetry, c->n, c->W, ks, vs, 0.0))
-      return fail(PP_ERR_SYMMETRY, "layer gate multiset is not invariant under the group");
+    for (int b = 0; b < c->B; ++b) {
+      std::vector<double> vs(n_gates);
+      for (int t = 0; t < n_gates; ++t) vs[t] = theta[(size_t)t * c->B + b];
+      if (!multiset_invariant(c->cfg.symmetry, c->n, c->W, ks, vs, 0.0))
+        return fail(PP_ERR_SYMMETRY, "layer gate multiset is not invariant under the group");
+    }
   }
   PP_TRY(ensure_merged(c));
   if (c->cfg.noise_mode == PP_NOISE_PER_LAYER && c->n_terms > 0) {
     PP_CUDA(launch_damp_layer(c->W, grid_for(c, c->n_terms, 4), c->stream,
-                              desc_of(c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
+                              desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
     c->launches += 1;
   }
   PP_TRY(make_room(c));
   const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
-  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0;
+  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0 && !c->batched;
+  if (c->batched && !args.empty()) PP_TRY(batched_columns(c, args, src_t, theta));
   int grid_b = 1;
   if (layered) {
     // persistent: one string per thread per pass, never more blocks than can
@@ -947,12 +1087,19 @@ pp_status pp_expect(pp_ctx* c, const double* bloch, double* out) {
     }
     a.sn_table = c->d_sn;
   }
-  PP_CUDA(launch_overlap(W, c->overlap_grid, c->stream, c->buf[c->active].keys,
-                         c->buf[c->active].coef, c->n_terms, nullptr, a, c->d_partials, c->d_out));
+  if (c->batched) {
+    PP_CUDA(launch_overlap_batched(W, c->overlap_grid, c->stream, desc_of(c, c->buf[c->active]),
+                                   c->n_terms, a, c->d_partials, c->d_out));
+  } else {
+    PP_CUDA(launch_overlap(W, c->overlap_grid, c->stream, c->buf[c->active].keys,
+                           c->buf[c->active].coef, c->n_terms, nullptr, a, c->d_partials,
+                           c->d_out));
+  }
   c->launches += 2;
-  PP_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PP_CUDA(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost,
+                          c->stream));
   PP_CUDA(cudaStreamSynchronize(c->stream));
-  *out = *c->h_out;
+  memcpy(out, c->h_out, sizeof(double) * c->B);
   return PP_OK;
 }
 
@@ -976,8 +1123,14 @@ pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, doubl
   Buf& d = c->buf[spare];
   // compact into the spare table without an index, then copy it out
   PP_TRY(ctl_prepare_insert(c, 0));
-  PP_CUDA(launch_compact(W, grid_for(c, c->n_terms, 4), c->stream, desc_of(c->buf[c->active]),
-                         c->n_terms, desc_of(d), 0, c->cfg.coeff_eps, 0.0, -1, c->d_ctl));
+  if (c->batched) {
+    PP_CUDA(launch_compact_batched(W, grid_for(c, c->n_terms, 4), c->stream,
+                                   desc_of(c, c->buf[c->active]), c->n_terms, desc_of(c, d), 0,
+                                   0.0, -1, c->d_ctl));
+  } else {
+    PP_CUDA(launch_compact(W, grid_for(c, c->n_terms, 4), c->stream, desc_of(c, c->buf[c->active]),
+                           c->n_terms, desc_of(c, d), 0, c->cfg.coeff_eps, 0.0, -1, c->d_ctl));
+  }
   c->launches += 1;
   PP_TRY(read_ctl(c));
   PP_TRY(check_device_error(c));
@@ -996,7 +1149,18 @@ pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, doubl
   std::vector<uint64_t> packed((size_t)m * 2 * W);
   PP_CUDA(cudaMemcpyAsync(packed.data(), d.keys, packed.size() * 8, cudaMemcpyDeviceToHost,
                           c->stream));
-  PP_CUDA(cudaMemcpyAsync(coef, d.coef, (size_t)m * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (c->batched) {
+    double* tmp = nullptr;
+    const size_t bytes = (size_t)m * c->B * sizeof(double);
+    PP_TRY(dmalloc(c, (void**)&tmp, bytes));
+    PP_CUDA(launch_rows_to_double(grid_for(c, (uint64_t)m * c->B, 4), c->stream, desc_of(c, d),
+                                  (uint64_t)m, tmp));
+    PP_CUDA(cudaMemcpyAsync(coef, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    dfree(c, tmp, bytes);
+  } else {
+    PP_CUDA(cudaMemcpyAsync(coef, d.coef, (size_t)m * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
   PP_CUDA(cudaStreamSynchronize(c->stream));
   for (int64_t i = 0; i < m; ++i)
     for (int j = 0; j < W; ++j) {

@@ -1,0 +1,431 @@
+// Device helpers shared by the CUDA translation units of the library: key
+// loads and stores, hashing, the key -> position index, the sign rule of a
+// Pauli product, orbit representatives and product-state overlaps.
+#pragma once
+
+#include "pp_internal.h"
+
+namespace ppk {
+namespace {
+
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSpinLimit = 1 << 22;
+
+template <int W>
+struct Key {
+  uint64_t w[2 * W];  // x[0..W), z[0..W)
+  __device__ __forceinline__ uint64_t& x(int i) { return w[i]; }
+  __device__ __forceinline__ uint64_t& z(int i) { return w[W + i]; }
+  __device__ __forceinline__ uint64_t x(int i) const { return w[i]; }
+  __device__ __forceinline__ uint64_t z(int i) const { return w[W + i]; }
+};
+
+template <int W>
+__device__ __forceinline__ Key<W> ld_key(const uint64_t* __restrict__ keys, uint64_t i) {
+  Key<W> k;
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ulonglong2 v = __ldg(p + j);
+    k.w[2 * j] = v.x;
+    k.w[2 * j + 1] = v.y;
+  }
+  return k;
+}
+
+// Load through L2 only (entries that other threads may have written in the
+// same kernel).
+template <int W>
+__device__ __forceinline__ Key<W> ld_key_cg(const uint64_t* keys, uint64_t i) {
+  Key<W> k;
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ulonglong2 v = __ldcg(p + j);
+    k.w[2 * j] = v.x;
+    k.w[2 * j + 1] = v.y;
+  }
+  return k;
+}
+
+template <int W>
+__device__ __forceinline__ void st_key(uint64_t* keys, uint64_t i, const Key<W>& k) {
+  ulonglong2* p = reinterpret_cast<ulonglong2*>(keys + i * (2 * W));
+#pragma unroll
+  for (int j = 0; j < W; ++j) p[j] = make_ulonglong2(k.w[2 * j], k.w[2 * j + 1]);
+}
+
+template <int W>
+__device__ __forceinline__ bool keys_equal(const Key<W>& a, const Key<W>& b) {
+  bool eq = true;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) eq &= (a.w[j] == b.w[j]);
+  return eq;
+}
+
+// 64-bit hash of a key built from 32-bit multiplies only (murmur3-style
+// mixing of the 32-bit halves, two lanes with different constants).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t key_hash(const Key<W>& k) {
+  uint32_t a = 0x9E3779B9u, b = 0x7F4A7C15u;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) {
+    const uint32_t lo = (uint32_t)k.w[j], hi = (uint32_t)(k.w[j] >> 32);
+    a = (a ^ lo) * 0xcc9e2d51u;
+    a = __funnelshift_l(a, a, 15) ^ hi;
+    a *= 0x1b873593u;
+    b = (b ^ hi) * 0x27d4eb2fu;
+    b = __funnelshift_l(b, b, 13) ^ lo;
+    b *= 0x165667b1u;
+  }
+  return ((uint64_t)fmix32(a ^ b) << 32) | fmix32(b + 0x9E3779B9u * a);
+}
+
+__device__ __forceinline__ uint32_t tag_of(uint64_t h) { return (uint32_t)(h >> 32) | 0x80000000u; }
+
+template <int W>
+__device__ __forceinline__ int weight(const Key<W>& k) {
+  int w = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) w += __popcll(k.x(j) | k.z(j));
+  return w;
+}
+
+// Find key k in the index.  Returns its dense position, -1 when it is not
+// present, or -2 (error bit set) when the probe bound is exhausted.
+template <int W>
+__device__ __forceinline__ int64_t index_find(const DevTable& t, const Key<W>& k, uint64_t h,
+                                              uint32_t tag, unsigned& err) {
+  uint64_t pos = h & t.imask;
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
+    if (s == 0) return -1;
+    if ((uint32_t)(s >> 32) == tag) {
+      uint32_t idx = (uint32_t)s;
+      if (idx != kPendingIdx && keys_equal(ld_key_cg<W>(t.keys, idx), k)) return (int64_t)idx;
+    }
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+  return -2;
+}
+
+// Claim an empty slot for a key whose dense position is already written.
+__device__ __forceinline__ void index_claim(const DevTable& t, uint64_t pos, uint64_t val,
+                                            unsigned& err) {
+  unsigned long long* idx = reinterpret_cast<unsigned long long*>(t.index);
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    if (atomicCAS(idx + pos, 0ull, (unsigned long long)val) == 0ull) return;
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------- gate kernel
+
+template <int W>
+__device__ __forceinline__ int sigma_of(const GateArgs& g, const Key<W>& q) {
+  // P Q = i^E R with E = sum_sites px pz + qx qz + 2 pz qx - (px^qx)(pz^qz)
+  // (P = i^{px pz} X^px Z^pz per site); i P Q = i^{E+1} R and E+1 is even.
+  int e = g.pyy;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    e += __popcll(q.x(j) & q.z(j)) + 2 * __popcll(g.pz[j] & q.x(j)) -
+         __popcll((g.px[j] ^ q.x(j)) & (g.pz[j] ^ q.z(j)));
+  }
+  return ((e + 1) & 3) == 0 ? 1 : -1;
+}
+
+__device__ __forceinline__ bool dead(double c, double eps) { return eps > 0.0 && c == 0.0; }
+__device__ __forceinline__ double trunc_c(double c, double eps) {
+  return (eps > 0.0 && !(fabs(c) >= eps)) ? 0.0 : c;
+}
+
+// The FP64 pipe of this GPU issues 2 instructions per cycle per SM, so the
+// gate kernel keeps it for the rotation arithmetic only: zero tests and
+// threshold compares run on the integer bit patterns (for finite doubles,
+// |a| < |b| exactly when (bits(a) & ~sign) < (bits(b) & ~sign) as unsigned).
+constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr uint64_t kSignBit = 0x8000000000000000ull;
+__device__ __forceinline__ uint64_t dbits(double c) { return (uint64_t)__double_as_longlong(c); }
+__device__ __forceinline__ bool is_zero_bits(double c) { return (dbits(c) << 1) == 0ull; }
+__device__ __forceinline__ double with_sign(double c, bool negate) {
+  return __longlong_as_double((long long)(dbits(c) ^ (negate ? kSignBit : 0ull)));
+}
+
+// -------------------------------------------------- canonicalisation
+
+// Digit word of Def. "Lowest integer representation": bit 2q = x_q ^ z_q,
+// bit 2q+1 = z_q, so the 2-bit digit of qubit q is I=0, X=1, Y=2, Z=3.
+__device__ __forceinline__ uint64_t spread32(uint32_t a) {
+  uint64_t x = a;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t compact64(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+__device__ __forceinline__ uint64_t digits32(uint32_t x, uint32_t z) {
+  return spread32(x ^ z) | (spread32(z) << 1);
+}
+
+// Z_n (Algorithm 2): min over the n translations of the 2n-bit digit integer.
+// T^j moves the letter of qubit q+j to qubit q, i.e. rotates the integer
+// right by 2j bits inside 2n bits.
+__device__ __forceinline__ void canon_zn_w1(Key<1>& k, int n) {
+  const uint64_t x = k.x(0), z = k.z(0);
+  if (n <= 32) {
+    const int nb = 2 * n;
+    const uint64_t mask = (nb == 64) ? ~0ull : ((1ull << nb) - 1ull);
+    const uint64_t v = digits32((uint32_t)x, (uint32_t)z);
+    uint64_t best = v;
+    for (int j = 1; j < n; ++j) {
+      const uint64_t r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
+      best = r < best ? r : best;
+    }
+    const uint32_t zz = compact64(best >> 1);
+    const uint32_t xz = compact64(best);
+    k.x(0) = (uint64_t)(xz ^ zz);
+    k.z(0) = (uint64_t)zz;
+    return;
+  }
+  typedef unsigned __int128 u128;
+  const int nb = 2 * n;
+  const u128 mask = (nb == 128) ? ~(u128)0 : (((u128)1 << nb) - 1);
+  const u128 v = (u128)digits32((uint32_t)x, (uint32_t)z) |
+                 ((u128)digits32((uint32_t)(x >> 32), (uint32_t)(z >> 32)) << 64);
+  u128 best = v;
+  for (int j = 1; j < n; ++j) {
+    const u128 r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
+    best = r < best ? r : best;
+  }
+  const uint64_t lo = (uint64_t)best, hi = (uint64_t)(best >> 64);
+  const uint64_t zz = (uint64_t)compact64(lo >> 1) | ((uint64_t)compact64(hi >> 1) << 32);
+  const uint64_t xz = (uint64_t)compact64(lo) | ((uint64_t)compact64(hi) << 32);
+  k.x(0) = xz ^ zz;
+  k.z(0) = zz;
+}
+
+template <int W>
+__device__ __forceinline__ int digit_at(const Key<W>& k, int q) {
+  const int xb = (int)((k.x(q >> 6) >> (q & 63)) & 1ull);
+  const int zb = (int)((k.z(q >> 6) >> (q & 63)) & 1ull);
+  return (zb << 1) | (xb ^ zb);
+}
+
+// Multi-word Z_n: compare translations digit by digit from the most
+// significant qubit and keep the smallest.
+template <int W>
+__device__ __forceinline__ void canon_zn_generic(Key<W>& k, int n) {
+  int best = 0;
+  for (int j = 1; j < n; ++j) {
+    int cmp = 0;
+    for (int q = n - 1; q >= 0 && cmp == 0; --q) {
+      int qa = q + j;
+      qa -= (qa >= n) ? n : 0;
+      int qb = q + best;
+      qb -= (qb >= n) ? n : 0;
+      const int a = digit_at<W>(k, qa), b = digit_at<W>(k, qb);
+      cmp = (a < b) ? -1 : ((a > b) ? 1 : 0);
+    }
+    if (cmp < 0) best = j;
+  }
+  if (best == 0) return;
+  Key<W> r;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
+  for (int q = 0; q < n; ++q) {
+    int src = q + best;
+    src -= (src >= n) ? n : 0;
+    const uint64_t xb = (k.x(src >> 6) >> (src & 63)) & 1ull;
+    const uint64_t zb = (k.z(src >> 6) >> (src & 63)) & 1ull;
+    r.x(q >> 6) |= xb << (q & 63);
+    r.z(q >> 6) |= zb << (q & 63);
+  }
+  k = r;
+}
+
+__device__ __forceinline__ uint64_t range_word(int w, int lo, int hi) {
+  int a = lo - 64 * w, b = hi - 64 * w;
+  a = a < 0 ? 0 : a;
+  b = b > 64 ? 64 : b;
+  if (b <= a) return 0ull;
+  const uint64_t upto_b = (b == 64) ? ~0ull : ((1ull << b) - 1ull);
+  const uint64_t below_a = (1ull << a) - 1ull;  // a < 64 here
+  return upto_b & ~below_a;
+}
+
+// S_n (Algorithm 3): count n_X, n_Y, n_Z and write Z^{nZ} Y^{nY} X^{nX} I...
+template <int W>
+__device__ __forceinline__ void canon_sn(Key<W>& k) {
+  int nx = 0, ny = 0, nz = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    nx += __popcll(k.x(j) & ~k.z(j));
+    ny += __popcll(k.x(j) & k.z(j));
+    nz += __popcll(k.z(j) & ~k.x(j));
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    k.z(j) = range_word(j, 0, nz + ny);
+    k.x(j) = range_word(j, nz, nz + ny + nx);
+  }
+}
+
+template <int W, int G>
+__device__ __forceinline__ void canon(Key<W>& k, int n) {
+  if constexpr (G == 1) {
+    if constexpr (W == 1) {
+      canon_zn_w1(k, n);
+    } else {
+      canon_zn_generic<W>(k, n);
+    }
+  } else if constexpr (G == 2) {
+    canon_sn<W>(k);
+  }
+}
+
+// ------------------------------------------------------------- overlap
+
+template <int W>
+__device__ __forceinline__ double overlap_plain(const Key<W>& k, const OverlapArgs& a) {
+  if (a.basis) {
+    uint64_t xo = 0;
+    int par = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      xo |= k.x(j);
+      par += __popcll(k.z(j) & a.bits[j]);
+    }
+    if (xo) return 0.0;
+    return (par & 1) ? -1.0 : 1.0;
+  }
+  double v = 1.0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    uint64_t m = k.x(j) | k.z(j);
+    while (m) {
+      const int b = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      const int q = 64 * j + b;
+      const int xb = (int)((k.x(j) >> b) & 1ull), zb = (int)((k.z(j) >> b) & 1ull);
+      const int l = xb ? (zb ? 1 : 0) : 2;  // X -> 0, Y -> 1, Z -> 2
+      v *= a.bloch[3 * q + l];
+    }
+  }
+  return v;
+}
+
+// Average of Tr[rho T^j r] over the n translations.
+template <int W>
+__device__ __forceinline__ double overlap_zn(const Key<W>& k, const OverlapArgs& a) {
+  const int n = a.n;
+  double acc = 0.0;
+  if (a.basis) {
+    uint64_t xo = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) xo |= k.x(j);
+    if (xo) return 0.0;
+    for (int s = 0; s < n; ++s) {
+      int par = 0;
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        uint64_t m = k.z(j);
+        while (m) {
+          const int b = __ffsll((long long)m) - 1;
+          m &= m - 1;
+          int q = 64 * j + b - s;
+          q += (q < 0) ? n : 0;
+          par += (int)((a.bits[q >> 6] >> (q & 63)) & 1ull);
+        }
+      }
+      acc += (par & 1) ? -1.0 : 1.0;
+    }
+    return acc / (double)n;
+  }
+  for (int s = 0; s < n; ++s) {
+    double v = 1.0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      uint64_t m = k.x(j) | k.z(j);
+      while (m) {
+        const int b = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        int q = 64 * j + b - s;
+        q += (q < 0) ? n : 0;
+        const int xb = (int)((k.x(j) >> b) & 1ull), zb = (int)((k.z(j) >> b) & 1ull);
+        const int l = xb ? (zb ? 1 : 0) : 2;
+        v *= a.bloch[3 * q + l];
+      }
+    }
+    acc += v;
+  }
+  return acc / (double)n;
+}
+
+template <int W>
+__device__ __forceinline__ double overlap_sn(const Key<W>& k, const OverlapArgs& a) {
+  int nx = 0, ny = 0, nz = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    nx += __popcll(k.x(j) & ~k.z(j));
+    ny += __popcll(k.x(j) & k.z(j));
+    nz += __popcll(k.z(j) & ~k.x(j));
+  }
+  const int S = a.n + 1;
+  return a.sn_table[((size_t)nx * S + ny) * S + nz];
+}
+
+__device__ __forceinline__ double ld_coef(const double* c, uint64_t i) { return __ldcg(c + i); }
+
+// Find key k among the entries that existed when the gate started (dense
+// position < T0); slots of this gate's births are skipped without reading
+// their keys, so births need no fence before they are published.
+template <int W>
+__device__ __forceinline__ int64_t index_find_old(const DevTable& t, const Key<W>& k, uint64_t h,
+                                                  uint32_t tag, uint64_t T0, unsigned& err) {
+  uint64_t pos = h & t.imask;
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    const uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
+    if (s == 0) return -1;
+    if ((uint32_t)(s >> 32) == tag) {
+      const uint32_t idx = (uint32_t)s;
+      if ((uint64_t)idx < T0 && keys_equal(ld_key_cg<W>(t.keys, idx), k)) return (int64_t)idx;
+    }
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+  return -2;
+}
+
+}  // namespace
+}  // namespace ppk

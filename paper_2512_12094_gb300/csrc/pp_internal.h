@@ -26,12 +26,20 @@ enum : unsigned {
 //   keys  [cap][2W]  x words then z words of each string
 //   coef  [cap]      FP64 coefficient; a truncated entry holds +0.0
 //   index [icap]     slot = (tag << 32) | dense position, 0 = empty
+// Batched tables (B angle sets, or FP32 storage) keep a row of B
+// coefficients per string in `rows` ([cap][B] of float or double) and a
+// liveness byte per string in `alive` instead of using `coef`: a row is dead
+// when every column was truncated, and readers treat a dead row as zeros.
 struct DevTable {
   uint64_t* keys;
   double* coef;
   uint64_t* index;
   uint64_t cap;
-  uint64_t imask;  // icap - 1, icap a power of two >= 2 cap
+  uint64_t imask;  // icap - 1, icap a power of two >= 1.5 cap
+  void* rows;
+  unsigned char* alive;
+  int B;
+  int f32;  // rows hold float (1) or double (0)
 };
 
 // Per-context counters in device memory.
@@ -74,6 +82,7 @@ struct GateArgs {
   uint64_t pvx[kMaxW], pvz[kMaxW];  // one bit of P (x or z plane): the pair member
                                     // with this bit clear owns the pair
   unsigned int gate_id;    // layer-local position in application order
+  const void* csb;         // batched: cos[B] then sin[B] of this gate (row element type)
 };
 
 struct OverlapArgs {
@@ -155,6 +164,29 @@ cudaError_t launch_pack_keys(int W, int n, int grid, cudaStream_t s, const uint6
 
 // Message returned by pp_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
+
+// ------------------------------------------------------- batched launchers
+// Same contracts as the single-column kernels above, on B-column rows.
+cudaError_t launch_gate_batched(int W, int f32, int grid, cudaStream_t s, const DevTable* tab,
+                                DevCtl* ctl, const GateArgs& g, bool pdl);
+// src rows: element type f32 (1) / double (0), or double input rows when
+// src_alive == nullptr (ingest); acc: [cap][B] doubles, zeroed by the caller.
+cudaError_t launch_merge_batched(int W, int group, int n, int wmax, int src_f32, int grid,
+                                 cudaStream_t s, const uint64_t* src_keys, const void* src_rows,
+                                 const unsigned char* src_alive, uint64_t count, DevTable dst,
+                                 double* acc, DevCtl* ctl);
+// acc rows -> dst rows (element type of dst), liveness by the any-column rule.
+cudaError_t launch_finalize_batched(int grid, cudaStream_t s, DevTable dst, const double* acc,
+                                    DevCtl* ctl, double eps);
+cudaError_t launch_compact_batched(int W, int grid, cudaStream_t s, DevTable src, uint64_t count,
+                                   DevTable dst, int with_index, double extra_eps,
+                                   int extra_wmax, DevCtl* ctl);
+// out[B] = sum over live strings of row * overlap; partials: [grid][B].
+cudaError_t launch_overlap_batched(int W, int grid, cudaStream_t s, DevTable t, uint64_t count,
+                                   const OverlapArgs& a, double* partials, double* out);
+// rows (any element type) -> doubles [count][B] (export)
+cudaError_t launch_rows_to_double(int grid, cudaStream_t s, DevTable t, uint64_t count,
+                                  double* out);
 
 int device_sm_count();
 int gate_blocks_per_sm(int W);  // resident gate-kernel blocks per SM

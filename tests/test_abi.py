@@ -47,12 +47,15 @@ def test_config_default(lib):
     assert cfg.check_symmetry == 1 and cfg.coeff_eps == 0.0
 
 
-@pytest.mark.parametrize("field,value", [("n_qubits", 0), ("n_qubits", 257), ("batch", 2),
-                                         ("symmetry", 3), ("coef_type", 1),
-                                         ("coeff_eps", -1.0), ("noise_mode", 7)])
-def test_create_rejects_bad_config_without_gpu(lib, field, value):
+@pytest.mark.parametrize("fields", [dict(n_qubits=0), dict(n_qubits=257), dict(batch=0),
+                                    dict(batch=513), dict(symmetry=3), dict(coef_type=2),
+                                    dict(coeff_eps=-1.0), dict(noise_mode=7),
+                                    dict(batch=4, noise_mode=2, noise_p=0.1),
+                                    dict(coef_type=1, noise_mode=2, noise_p=0.1)])
+def test_create_rejects_bad_config_without_gpu(lib, fields):
     cfg = pp.pp_config_default(n_qubits=8)
-    setattr(cfg, field, value)
+    for field, value in fields.items():
+        setattr(cfg, field, value)
     h = ctypes.c_void_p()
     st = lib.pp_create(ctypes.byref(cfg), 0, None, None, None, ctypes.byref(h))
     assert st == 1  # PP_ERR_ARG

@@ -354,3 +354,75 @@ def test_s2_invariant_for_symmetric_heisenberg_a2a(oracle_lib):
     wl.state = pi.plus_state(n)
     _, vals = oracle_lib.run_workload(wl, record_each_step=True)
     np.testing.assert_allclose(vals, [n * (n + 2) / 4] * 2, rtol=1e-12)
+
+
+# ------------------------------------------------------ batched angle sets
+
+def _ring_angles(B, seed):
+    return pi.batched_ring_angles(B, seed)
+
+
+def _ring_theta(n, angles):
+    """[K=3n, B] angles of one ring layer for B angle triples (theta_J, theta_x, theta_z)."""
+    B = len(angles)
+    th = np.zeros((3 * n, B))
+    th[:n] = angles[:, 0]
+    th[n:2 * n] = angles[:, 1]
+    th[2 * n:] = angles[:, 2]
+    return th
+
+
+def test_batched_columns_equal_single_runs_bitexact(oracle_lib):
+    n, B, L = 6, 5, 3
+    angles = _ring_angles(B, 3)
+    gx, gz, _ = pi.Circuit(n, [pi.ring_layer(n, 0, 0, 0)]).gate_arrays(0)
+    obs = pi.mean_z(n)
+    x, z, c = obs.arrays()
+    bst = oracle_lib.BatchedOracleState(n, B, x, z, np.repeat(c[:, None], B, axis=1))
+    th = _ring_theta(n, angles)
+    for _ in range(L):
+        bst.apply_layer(gx, gz, th)
+    bx, bz, bc = bst.export()
+    bkeys = [tuple(a) + tuple(b) for a, b in zip(bx.tolist(), bz.tolist())]
+    for b in range(B):
+        st = oracle_lib.OracleState(n, x, z, c)
+        for _ in range(L):
+            st.apply_layer(gx, gz, th[:, b])
+        want = st.as_dict()
+        got = {k: bc[i, b] for i, k in enumerate(bkeys)}
+        assert set(want) <= set(got)
+        for k, v in got.items():
+            assert v == want.get(k, 0.0)
+    ref = sv.statevector_expectations(
+        [[(s, angles[1][0] if g < n else (angles[1][1] if g < 2 * n else angles[1][2]))
+          for g, (s, _) in enumerate(pi.ring_layer(n, 0, 0, 0))]] * L,
+        obs.terms, pi.zero_state(n).bloch)[-1]
+    assert bst.expect(pi.zero_state(n).bloch)[1] == pytest.approx(ref, abs=1e-12)
+
+
+def test_batched_single_column_equals_single_state_with_truncation(oracle_lib):
+    n = 10
+    wl = pi.config1_ring(n=n, steps=4, eps=1e-3, max_weight=5)
+    x, z, c = wl.observable.arrays()
+    bst = oracle_lib.BatchedOracleState(n, 1, x, z, c[:, None], eps=wl.eps,
+                                        max_weight=wl.max_weight)
+    st = oracle_lib.OracleState(n, x, z, c, eps=wl.eps, max_weight=wl.max_weight)
+    for layer in range(4):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        bst.apply_layer(gx, gz, th[:, None])
+        st.apply_layer(gx, gz, th)
+    bx, bz, bc = bst.export()
+    sx, sz, sc = st.export()
+    np.testing.assert_array_equal(bx, sx)
+    np.testing.assert_array_equal(bz, sz)
+    np.testing.assert_array_equal(bc[:, 0], sc)
+
+
+def test_batched_truncation_keeps_a_term_if_any_column_is_large(oracle_lib):
+    n = 3
+    x, z = pi.to_masks(["ZII", "XII", "IYI"], n)
+    coef = np.array([[1e-4, 2e-2], [1e-4, 1e-4], [0.5, 0.5]])
+    bst = oracle_lib.BatchedOracleState(n, 2, x, z, coef, eps=1e-2)
+    bx, bz, bc = bst.export()
+    got = dict(zip(pi.from_masks(bx, bz, n), map(tuple, bc)))
+    assert got == {"ZII": (1e-4, 2e-2), "IYI": (0.5, 0.5)}
