@@ -37,6 +37,10 @@ METRIC = "pauli_term_gate_updates_per_s"
 UNIT = "updates/s"
 KEY_BYTES = 16   # one uint64 X word + one uint64 Z word (n = 32)
 COEF_BYTES = 8   # FP64
+# DRAM bytes (read + write) per algorithmic byte of layer_kernel<1>, from the
+# ncu capture of one full layer of this workload summarised in
+# profiles/layer_kernel_ring32_zn_layer19.md (5.299 GB / 4.338 GB).
+TRAFFIC_PER_ALG_BYTE = 1.22
 
 
 def peaks():
@@ -185,8 +189,11 @@ def bench_ours(args):
         ms_total, upd, launches = 0.0, 0.0, 0
         split = [0.0, 0.0]
         vals = stats = None
+        ac = gate_ms = 0.0
+        gate_n = 0
         for _ in range(args.steps):
-            vals, stats, ev = timed_job(False, args.profile_timed)
+            # the layer kernels are bracketed by CUDA events on the job's stream
+            vals, stats, ev = timed_job(False, True)
             ms_total += ev[0].elapsed_time(ev[2])
             if args.only == "both":
                 split[0] += ev[0].elapsed_time(ev[1])
@@ -194,6 +201,9 @@ def bench_ours(args):
             for st in stats:
                 upd += st["gate_updates"]
                 launches += st["kernel_launches"]
+                ac += st["anticommuting_terms"]
+                gate_ms += st["gate_kernel_ms"]
+                gate_n += st["gate_kernels_timed"]
         clk = clocks.stop()
         barrier()
         # end to end through the host-buffer API (inputs copied in, result read back)
@@ -202,13 +212,7 @@ def bench_ours(args):
             for _ in range(args.steps):
                 _, _, ev = timed_job(True, False)
                 e2e_ms += ev[0].elapsed_time(ev[2])
-        # roofline pass: the same job once more, every gate kernel bracketed
-        # by CUDA events on the context's stream
-        _, pstats, _ = timed_job(False, True)
-    ac = sum(st["anticommuting_terms"] for st in pstats)
-    pupd = sum(st["gate_updates"] for st in pstats)
-    gate_ms = sum(st["gate_kernel_ms"] for st in pstats)
-    gate_n = sum(st["gate_kernels_timed"] for st in pstats)
+    pupd = upd
 
     t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
     if dist is not None:
@@ -241,18 +245,22 @@ def bench_ours(args):
                    "l2": "flushed (256 MB write) before every timed job",
                    "parallelism": "replicas" if world > 1 else "single"},
         "breakdown_ms_per_step": {"plain": split[0] / args.steps, "zn": split[1] / args.steps,
-                                  "gate_kernels_profiled_job": gate_ms},
+                                  "layer_kernels": gate_ms / args.steps},
         "result": {"expect": vals, "live_terms": [st["live_terms"] for st in stats]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                     "kernel": "gate_kernel<1>", "peak_kind": peak_kind,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": TRAFFIC_PER_ALG_BYTE * bytes_alg / max(gate_n, 1),
+                     "traffic_basis": "ncu DRAM bytes per algorithmic byte of one full layer "
+                                      "(profiles/layer_kernel_ring32_zn_layer19.md) x this "
+                                      "average launch",
+                     "kernel": "layer_kernel<1>", "peak_kind": peak_kind,
                      "bytes_model": "16 B key per live term + 64 B per live anticommuting term",
                      "avg_launch_us": 1e3 * gate_ms / max(gate_n, 1),
                      "algorithmic_bytes_per_launch": bytes_alg / max(gate_n, 1),
-                     "timing": "CUDA events around every gate kernel of one extra job"},
+                     "timing": "CUDA events around every layer kernel in the timed steps"},
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -360,8 +368,6 @@ def main():
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
-    ap.add_argument("--profile-timed", action="store_true",
-                    help="also bracket every gate kernel with events inside the timed steps")
     args = ap.parse_args()
     if args.profile_layer >= 0:
         profile_layer(args)
