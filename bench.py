@@ -335,6 +335,93 @@ def profile_layer(args):
     pp.pp_destroy(ctx)
 
 
+A2A_N = {16: 8, 32: 10, 64: 12, 128: 16}
+
+
+def serving_specs(n_jobs, rate, seed=0):
+    """The Poisson job stream of the serving workload, scaled so that every
+    job finishes in well under a second: ring jobs keep n in {16..128} with
+    steps <= 20, weight <= 8 and eps >= 1e-4; all-to-all jobs use n in
+    {8, 10, 12, 16} (mapped from {16, 32, 64, 128}) and <= 4 steps."""
+    out = []
+    for j in pi.serving_stream(n_jobs, rate, seed):
+        a = j["angles"]
+        eps = max(j["eps"], 1e-4)
+        if j["family"] == "ring":
+            wl = pi.config1_ring(n=j["n"], steps=min(j["steps"], 20), theta_j=a[0], theta_x=a[1],
+                                 theta_z=a[2], eps=eps, max_weight=8, symmetry=j["group"])
+        else:
+            n = A2A_N[j["n"]]
+            wl = pi.config0_heisenberg(n=n, dt=0.02 + 0.02 * a[0], steps=min(j["steps"], 4))
+            wl.observable = pi.mean_z(n)
+            wl.state = pi.neel_state(n)
+            wl.eps = eps
+            wl.symmetry = j["group"]
+        out.append((j["arrival"], wl))
+    return out
+
+
+def bench_serving(args):
+    import torch
+    import paper_2512_12094_gb300 as pp
+    torch.cuda.set_device(0)
+    pp.build()
+    pp.load()
+    specs = serving_specs(args.serving, args.rate)
+    jobs = []
+    for _, wl in specs:
+        cfg = pp.pp_config_default(n_qubits=wl.circuit.n, symmetry=wl.symmetry, coeff_eps=wl.eps,
+                                   max_weight=wl.max_weight)
+        x, z, c = wl.observable.arrays()
+        gx, gz, th = wl.circuit.gate_arrays(0)
+        jobs.append(pp.make_job(cfg, x, z, c, pp.pack_gates(gx, gz), th, len(wl.circuit.layers),
+                                wl.state.bloch, True, 256 << 20))
+
+    def run(slots, paced):
+        server = pp.pp_server_create(slots, 150 << 30, 256 << 20)
+        t0 = time.perf_counter()
+        ids = []
+        for (arrival, _), (job, _bufs) in zip(specs, jobs):
+            if paced:
+                delay = t0 + arrival - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            ids.append(pp.pp_submit(server, job))
+        res = [pp.pp_server_wait(server, i) for i in ids]
+        t1 = time.perf_counter()
+        pp.pp_server_destroy(server)
+        return res, t1 - t0
+
+    def report_failures(tag, res):
+        bad = [r for r in res if r["status"] != 0]
+        if bad:
+            hist = {}
+            for r in bad:
+                hist[r["status"]] = hist.get(r["status"], 0) + 1
+            print(f"{tag}: {len(bad)} failed jobs, statuses {hist}; first: {bad[0]['message']}",
+                  file=sys.stderr, flush=True)
+
+    warm, _ = run(args.slots, False)  # warm-up (builds graphs, pools)
+    report_failures("warm-up", warm)
+    res, wall = run(args.slots, True)
+    report_failures("timed", res)
+    lat = np.array([r["latency_ms"] for r in res])
+    seq, seq_wall = run(1, False)  # plain per-job propagation, one after the other
+    err = max(abs(a["value"] - b["value"]) for a, b in zip(res, seq))
+    line = {"metric": "served_jobs_per_s", "value": len(res) / wall, "unit": "jobs/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "serving_stream_scaled", "jobs": len(res), "rate_per_s": args.rate,
+                       "slots": args.slots, "budget_bytes": 150 << 30},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "run_ms": {"p50": float(np.percentile([r["run_ms"] for r in res], 50))},
+            "failed": int(sum(r["status"] != 0 for r in res)),
+            "sequential_per_job": {"jobs_per_s": len(seq) / seq_wall, "wall_s": seq_wall},
+            "offered_load_wall_s": float(specs[-1][0]),
+            "max_abs_diff_vs_sequential": err}
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """The oracle as the reference arm, on the host cores (rank 0 only)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -366,10 +453,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--serving", type=int, default=0,
+                    help="serve N jobs of the scaled Poisson stream instead of the main job")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     args = ap.parse_args()
-    if args.profile_layer >= 0:
+    if args.serving > 0:
+        bench_serving(args)
+    elif args.profile_layer >= 0:
         profile_layer(args)
     elif args.impl == "reference":
         bench_reference(args)

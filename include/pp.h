@@ -222,6 +222,76 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* keys,
                          const double* coef, const double* bloch, double* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving (continuous batching of independent propagation jobs).  The paper
+ * has no counterpart; a job is the Algorithm 1 computation of one request.
+ * ------------------------------------------------------------------------ */
+
+typedef struct pp_server pp_server;
+
+/* One request: O (x, z [n_terms][W], coef [n_terms][cfg.batch]), one layer of
+ * gates in time order (gates [n_layer_gates], theta [n_layer_gates][batch])
+ * applied n_layers times (Trotter steps; pp_apply_layer semantics, with the
+ * symmetry merge after each layer when symmetric_boundary != 0), and the
+ * product state bloch [n][3].  cfg.cuda_stream and cfg.mem_budget_bytes are
+ * set by the server.  mem_bytes: device memory reserved for the job while it
+ * runs (0 = the server's default); a job that needs more is retried with four
+ * times the reservation, up to the server budget.  All arrays are copied by
+ * pp_submit. */
+typedef struct {
+  pp_config cfg;
+  int64_t n_terms;
+  const uint64_t* x;
+  const uint64_t* z;
+  const double* coef;
+  int n_layer_gates;
+  const pp_pauli* gates;
+  const double* theta;
+  int n_layers;
+  int symmetric_boundary;
+  const double* bloch;
+  size_t mem_bytes;
+} pp_job;
+
+typedef struct {
+  int done;             /* 0 while queued or running */
+  int status;           /* pp_status of the job */
+  double value;         /* Tr[rho O_0] (first angle set) */
+  int64_t live_terms;
+  double gate_updates;
+  size_t device_bytes;  /* peak-time device memory of the job's context */
+  size_t reserved_bytes;
+  double queue_ms;      /* submit -> start */
+  double run_ms;        /* start -> finish */
+  double latency_ms;    /* submit -> finish */
+  char message[160];    /* the failing call's error text when status != PP_OK */
+} pp_job_result;
+
+/* A server with `slots` worker threads, each owning a CUDA stream on the
+ * calling thread's current device.  Jobs are admitted oldest first among
+ * those whose reservation fits in mem_budget_bytes minus the reservations of
+ * running jobs; their kernels overlap on the device.  default_job_bytes = 0
+ * picks 64 MiB.  Errors: PP_ERR_ARG, PP_ERR_CUDA. */
+pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_job_bytes,
+                           pp_server** out);
+
+/* Queue a job (thread-safe); *job_id identifies it.  PP_ERR_REJECTED when its
+ * reservation can never fit the budget, PP_ERR_ARG for a malformed job. */
+pp_status pp_submit(pp_server* server, const pp_job* job, uint64_t* job_id);
+
+/* Result so far (done = 0 while pending); PP_ERR_ARG for an unknown id. */
+pp_status pp_server_poll(pp_server* server, uint64_t job_id, pp_job_result* out);
+
+/* Block until the job is done. */
+pp_status pp_server_wait(pp_server* server, uint64_t job_id, pp_job_result* out);
+
+/* Queue length, running jobs, completed jobs, reserved bytes (any may be NULL). */
+pp_status pp_server_stats(pp_server* server, int64_t* queued, int64_t* running,
+                          int64_t* completed, size_t* reserved_bytes);
+
+/* Finish every queued job, then stop the workers and free the server. */
+pp_status pp_server_destroy(pp_server* server);
+
 /* pp_merge_terms without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while they run -- a serving loop whose memory is fixed at

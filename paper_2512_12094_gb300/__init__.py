@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _LIB = os.path.join(_HERE, "libpp.so")
-_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu", "pp_batched.cu"]
+_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu", "pp_batched.cu", "pp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -89,6 +89,26 @@ class pp_config(ctypes.Structure):
                 ("layer_kernel", ctypes.c_int)]
 
 
+class pp_pauli(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint64 * 4), ("z", ctypes.c_uint64 * 4)]
+
+
+class pp_job(ctypes.Structure):
+    _fields_ = [("cfg", pp_config), ("n_terms", ctypes.c_int64), ("x", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("n_layer_gates", ctypes.c_int),
+                ("gates", ctypes.c_void_p), ("theta", ctypes.c_void_p), ("n_layers", ctypes.c_int),
+                ("symmetric_boundary", ctypes.c_int), ("bloch", ctypes.c_void_p),
+                ("mem_bytes", ctypes.c_size_t)]
+
+
+class pp_job_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("value", ctypes.c_double),
+                ("live_terms", ctypes.c_int64), ("gate_updates", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("reserved_bytes", ctypes.c_size_t),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("message", ctypes.c_char * 160)]
+
+
 class pp_stats_t(ctypes.Structure):
     _fields_ = [("live_terms", ctypes.c_int64), ("stored_terms", ctypes.c_int64),
                 ("capacity", ctypes.c_int64), ("gate_updates", ctypes.c_double),
@@ -127,6 +147,12 @@ _SIGS = {
     "pp_overlap_sum": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp],
     "pp_merge_terms_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                _vp],
+    "pp_server_create": [ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp)],
+    "pp_submit": [_vp, ctypes.POINTER(pp_job), ctypes.POINTER(ctypes.c_uint64)],
+    "pp_server_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(pp_job_result)],
+    "pp_server_wait": [_vp, ctypes.c_uint64, ctypes.POINTER(pp_job_result)],
+    "pp_server_stats": [_vp, _i64p, _i64p, _i64p, ctypes.POINTER(ctypes.c_size_t)],
+    "pp_server_destroy": [_vp],
 }
 _RESTYPE = {"pp_last_error": ctypes.c_char_p}
 
@@ -307,6 +333,66 @@ def pp_merge_terms_noalloc(n_qubits: int, symmetry: int, m: int, keys_in, coef_i
     _check(load().pp_merge_terms_noalloc(n_qubits, symmetry, int(m), _ptr(keys_in), _ptr(coef_in),
                                          _ptr(keys_out), _ptr(coef_out), _ptr(m_out_dev),
                                          _stream(stream)))
+
+
+def pp_server_create(slots: int, mem_budget_bytes: int, default_job_bytes: int = 0):
+    h = _vp()
+    _check(load().pp_server_create(int(slots), int(mem_budget_bytes), int(default_job_bytes),
+                                   ctypes.byref(h)))
+    return h
+
+
+def pp_server_destroy(server):
+    _check(load().pp_server_destroy(server))
+
+
+def make_job(cfg: pp_config, x, z, coef, gates_packed, theta, n_layers: int, bloch,
+             symmetric_boundary: bool = True, mem_bytes: int = 0):
+    """Build a pp_job; the returned tuple keeps the numpy buffers alive."""
+    W = (cfg.n_qubits + 63) // 64
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64).reshape(-1, W))
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.uint64).reshape(-1, W))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, cfg.batch))
+    g = np.ascontiguousarray(gates_packed)
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(bloch, dtype=np.float64).reshape(-1))
+    job = pp_job(cfg=cfg, n_terms=c.shape[0], x=_ptr(x), z=_ptr(z), coef=_ptr(c),
+                 n_layer_gates=g.shape[0], gates=_ptr(g), theta=_ptr(th), n_layers=int(n_layers),
+                 symmetric_boundary=int(bool(symmetric_boundary)), bloch=_ptr(b),
+                 mem_bytes=int(mem_bytes))
+    return job, (x, z, c, g, th, b)
+
+
+def pp_submit(server, job: "pp_job") -> int:
+    jid = ctypes.c_uint64()
+    _check(load().pp_submit(server, ctypes.byref(job), ctypes.byref(jid)))
+    return jid.value
+
+
+def _result(r: "pp_job_result") -> dict:
+    out = {k: getattr(r, k) for k, _ in pp_job_result._fields_}
+    out["message"] = r.message.decode(errors="replace")
+    return out
+
+
+def pp_server_poll(server, job_id: int) -> dict:
+    r = pp_job_result()
+    _check(load().pp_server_poll(server, int(job_id), ctypes.byref(r)))
+    return _result(r)
+
+
+def pp_server_wait(server, job_id: int) -> dict:
+    r = pp_job_result()
+    _check(load().pp_server_wait(server, int(job_id), ctypes.byref(r)))
+    return _result(r)
+
+
+def pp_server_stats(server) -> dict:
+    q, r, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    b = ctypes.c_size_t()
+    _check(load().pp_server_stats(server, ctypes.byref(q), ctypes.byref(r), ctypes.byref(c),
+                                  ctypes.byref(b)))
+    return {"queued": q.value, "running": r.value, "completed": c.value, "reserved_bytes": b.value}
 
 
 def _stream(s):

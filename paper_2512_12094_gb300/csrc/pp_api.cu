@@ -199,12 +199,22 @@ DevTable desc_of(const pp_ctx* c, const Buf& b) {
   return t;
 }
 
-// Write the descriptors of both tables and the active copy (synchronous
-// copy from host memory; only called when a table is (re)allocated).
+// Host to device copy ordered on the context's stream, complete on return.
+// A plain cudaMemcpy from pageable memory goes through the legacy default
+// stream and may return before its DMA lands; kernels on a non-blocking
+// stream do not wait for it and could read what was there before (in a
+// server, memory another job just freed).
+cudaError_t upload(pp_ctx* c, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+// Write the descriptors of both tables and the active copy (only called when
+// a table is (re)allocated).
 pp_status publish_desc(pp_ctx* c) {
   DevTable h[3] = {desc_of(c, c->buf[0]), desc_of(c, c->buf[1]), desc_of(c, c->buf[c->active])};
-  PP_CUDA(cudaStreamSynchronize(c->stream));
-  PP_CUDA(cudaMemcpy(c->d_desc, h, sizeof(h), cudaMemcpyHostToDevice));
+  PP_CUDA(upload(c, c->d_desc, h, sizeof(h)));
   return PP_OK;
 }
 
@@ -508,13 +518,12 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
     std::vector<double> damp(c->n + 1, 1.0), ldamp(c->n + 1, 1.0);
     for (int k = 1; k <= c->n; ++k) damp[k] = damp[k - 1] * (1.0 - cfg->noise_p);
     for (int k = 0; k <= c->n; ++k) ldamp[k] = std::exp(-cfg->noise_p * (double)k);
-    cudaStreamSynchronize(c->stream);
-    if (cudaMemcpy(c->d_damp, damp.data(), damp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->d_ldamp, ldamp.data(), ldamp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (upload(c, c->d_damp, damp.data(), damp.size() * 8) != cudaSuccess ||
+        upload(c, c->d_ldamp, ldamp.data(), ldamp.size() * 8) != cudaSuccess)
       return cleanup(fail(PP_ERR_CUDA, "constant table upload failed"));
     DevCtl zero;
     memset(&zero, 0, sizeof(zero));
-    if (cudaMemcpy(c->d_ctl, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (upload(c, c->d_ctl, &zero, sizeof(zero)) != cudaSuccess)
       return cleanup(fail(PP_ERR_CUDA, "control block init failed"));
   }
   uint64_t cap = std::max<uint64_t>(4 * (uint64_t)n_terms, 1024);
@@ -700,8 +709,7 @@ pp_status cached_upload(pp_ctx* c, std::vector<ArgsEntry>& cache,
   ArgsEntry ent;
   ent.n = bytes.size();
   PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n));
-  PP_CUDA(cudaStreamSynchronize(c->stream));
-  PP_CUDA(cudaMemcpy(ent.d_args, bytes.data(), ent.n, cudaMemcpyHostToDevice));
+  PP_CUDA(upload(c, ent.d_args, bytes.data(), ent.n));
   ent.sig = std::move(bytes);
   ent.last_use = c->graph_clock;
   *out = ent.d_args;
@@ -850,8 +858,7 @@ pp_status device_args(pp_ctx* c, const std::vector<GateArgs>& args, const GateAr
   ArgsEntry ent;
   ent.n = args.size();
   PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n * sizeof(GateArgs)));
-  PP_CUDA(cudaStreamSynchronize(c->stream));
-  PP_CUDA(cudaMemcpy(ent.d_args, args.data(), ent.n * sizeof(GateArgs), cudaMemcpyHostToDevice));
+  PP_CUDA(upload(c, ent.d_args, args.data(), ent.n * sizeof(GateArgs)));
   ent.sig = std::move(sig);
   ent.last_use = c->graph_clock;
   *out = ent.d_args;
