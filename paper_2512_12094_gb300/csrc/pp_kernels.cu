@@ -30,9 +30,22 @@ namespace {
 // staging area fills up appends the rest directly, one atomic per warp.
 template <int W>
 struct GateStage {
-  static constexpr int kCap = (W <= 2) ? 512 : 256;
+  static constexpr int kCap = (W == 1) ? 512 : ((W <= 3) ? 256 : 128);
   uint64_t key[kCap][2 * W];
   double coef[kCap];
+};
+
+// Per-warp worklist.  A warp scans kU strings per lane (all loads in flight
+// at once), keeps the anticommuting ones (key and offset in the warp's chunk)
+// here, then works through the list with every lane busy: the dependent
+// lookup chain (index slot -> partner key -> coefficients) then runs once per
+// 32 anticommuting strings instead of once per 32 scanned strings.
+template <int W>
+struct GateList {
+  static constexpr int kU = (W <= 2) ? 4 : 2;
+  static constexpr int kItems = 32 * kU;
+  uint64_t key[kBlock / 32][kItems][2 * W];
+  unsigned short off[kBlock / 32][kItems];
 };
 
 struct GateShared {
@@ -51,10 +64,12 @@ template <int W>
 __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const GateArgs& g,
                                           uint64_t T0, unsigned long long* cnt_slot,
                                           long long* dlt_slot, GateStage<W>& stage,
-                                          GateShared& sh) {
+                                          GateList<W>& list, GateShared& sh) {
   constexpr int kWarps = kBlock / 32;
+  constexpr int kU = GateList<W>::kU;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
   const bool noise = g.damp != nullptr;
   const bool use_eps = g.use_eps != 0;
   const uint64_t eps_bits = g.eps_bits;
@@ -64,23 +79,51 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
   long long delta = 0;
   unsigned long long n_ac = 0;  // live anticommuting terms (for the byte model)
   unsigned err = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  // warp-uniform trip count: every lane reaches the ballots below
-  for (uint64_t base = (uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u); base < T0;
-       base += stride) {
-    const uint64_t i = base + lane;
-    bool want = false;
-    double child = 0.0;
-    if (i < T0) {
-      const Key<W> Q = ld_key_cg<W>(t.keys, i);
-      int acnt = 0, kq = 0;
+  // Block b takes the contiguous range [T0 b / G, T0 (b+1) / G) and splits it
+  // into nt equal tiles of at most kBlock * kU strings, each split equally
+  // over the warps: every block does the same number of equally sized tiles,
+  // so blocks reach the grid barrier together, and a small table spreads one
+  // string per lane over all warps.  nt is block-uniform, so every lane of a
+  // warp reaches the ballots below.
+  const uint64_t G = gridDim.x;
+  const uint64_t b0 = T0 * blockIdx.x / G;
+  const uint64_t Rn = T0 * (blockIdx.x + 1) / G - b0;
+  constexpr uint64_t kTileMax = (uint64_t)kBlock * kU;
+  const uint64_t nt = (Rn + kTileMax - 1) / kTileMax;
+  auto warp_range = [&](uint64_t tt, uint64_t& ws, uint64_t& we) {
+    const uint64_t ts = b0 + Rn * tt / nt, te = b0 + Rn * (tt + 1) / nt;
+    ws = ts + (te - ts) * warp / kWarps;  // at most 32 kU strings per warp
+    we = ts + (te - ts) * (warp + 1) / kWarps;
+  };
+  Key<W> Q[kU];
+  auto load_tile = [&](uint64_t ws, uint64_t we) {
 #pragma unroll
-      for (int j = 0; j < W; ++j) {
-        acnt += __popcll(g.px[j] & Q.z(j)) + __popcll(g.pz[j] & Q.x(j));
-        if (noise) kq += __popcll((Q.x(j) | Q.z(j)) & g.supp[j]);
-      }
-      if ((acnt & 1) == 0) {
-        if (noise && kq) {  // commuting term: damping only
+    for (int u = 0; u < kU; ++u) {
+      const uint64_t i = ws + (uint64_t)(u * 32 + lane);
+      if (i < we) Q[u] = ld_key_cg<W>(t.keys, i);
+    }
+  };
+  uint64_t ws = 0, we = 0;
+  if (nt > 0) {
+    warp_range(0, ws, we);
+    load_tile(ws, we);
+  }
+  for (uint64_t tt = 0; tt < nt; ++tt) {
+    // ---- phase A: test the loaded strings, compact the anticommuting ones
+    unsigned n_items = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint64_t i = ws + (uint64_t)(u * 32 + lane);
+      bool ac = false;
+      if (i < we) {
+        int acnt = 0, kq = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          acnt += __popcll(g.px[j] & Q[u].z(j)) + __popcll(g.pz[j] & Q[u].x(j));
+          if (noise) kq += __popcll((Q[u].x(j) | Q[u].z(j)) & g.supp[j]);
+        }
+        ac = (acnt & 1) != 0;
+        if (!ac && noise && kq) {  // commuting term: damping only
           const double c = ld_coef(t.coef, i);
           if (!is_dead(c)) {
             const double d = trunc(__dmul_rn(c, g.damp[kq]));
@@ -88,18 +131,46 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
             t.coef[i] = d;
           }
         }
-      } else {
-        Key<W> R;
+      }
+      const unsigned bal = __ballot_sync(kFull, ac);
+      if (ac) {
+        const unsigned p = n_items + __popc(bal & lanes_below);
+#pragma unroll
+        for (int j = 0; j < 2 * W; ++j) list.key[warp][p][j] = Q[u].w[j];
+        list.off[warp][p] = (unsigned short)(u * 32 + lane);
+      }
+      n_items += __popc(bal);
+    }
+    __syncwarp();
+    const uint64_t wb = ws;  // offsets in the list are relative to this
+    // the next tile's keys load while this tile's list is worked through
+    if (tt + 1 < nt) {
+      warp_range(tt + 1, ws, we);
+      load_tile(ws, we);
+    }
+    // ---- phase B: the anticommuting strings, one per lane
+    for (unsigned k0 = 0; k0 < n_items; k0 += 32) {
+      const unsigned k = k0 + lane;
+      bool want = false;
+      double child = 0.0;
+      uint64_t i = 0;
+      Key<W> R;
+      if (k < n_items) {
+        Key<W> Qk;
+#pragma unroll
+        for (int j = 0; j < 2 * W; ++j) Qk.w[j] = list.key[warp][k][j];
+        i = wb + list.off[warp][k];
+        int kq = 0;
+        uint64_t pw = 0;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-          R.x(j) = Q.x(j) ^ g.px[j];
-          R.z(j) = Q.z(j) ^ g.pz[j];
+          R.x(j) = Qk.x(j) ^ g.px[j];
+          R.z(j) = Qk.z(j) ^ g.pz[j];
+          if (noise) kq += __popcll((Qk.x(j) | Qk.z(j)) & g.supp[j]);
+          pw |= (Qk.x(j) & g.pvx[j]) | (Qk.z(j) & g.pvz[j]);
         }
         const double cQ = ld_coef(t.coef, i);
         const bool liveQ = !is_dead(cQ);
-        uint64_t pw = 0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) pw |= (Q.x(j) & g.pvx[j]) | (Q.z(j) & g.pvz[j]);
         // The member of {Q, R} with the pivot bit of P clear owns the pair,
         // decided from keys only.  A truncated member with the bit set has
         // nothing to do (its partner either owns the pair or is absent), so it
@@ -111,82 +182,80 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
           jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
         }
         n_ac += liveQ;
-        const bool neg = sigma_of<W>(g, Q) < 0;  // i P Q = -R
-        if (jr >= 0) {
-          const double cR = pw == 0 ? ld_coef(t.coef, jr) : 0.0;
-          if (pw == 0 && (liveQ || !is_dead(cR))) {  // this thread owns the pair
-            double dQ = cQ, dR = cR;
-            if (noise) {
-              int kr = 0;
+        const bool neg = sigma_of<W>(g, Qk) < 0;  // i P Q = -R
+        const double cR = (jr >= 0 && pw == 0) ? ld_coef(t.coef, jr) : 0.0;
+        // owner with its partner stored, or a live string whose partner is new
+        const bool own = jr >= 0 && pw == 0 && (liveQ || !is_dead(cR));
+        const bool birth = jr == -1 && liveQ;
+        if (own || birth) {
+          // one instruction sequence for both cases (a birth has c_R = 0 and
+          // uses only the products of c_Q); the FP64 pipe is narrow here
+          double dQ = cQ, dR = cR;
+          if (noise) {
+            int kr = 0;
 #pragma unroll
-              for (int j = 0; j < W; ++j) kr += __popcll((R.x(j) | R.z(j)) & g.supp[j]);
-              if (kq) dQ = __dmul_rn(dQ, g.damp[kq]);
-              if (kr) dR = __dmul_rn(dR, g.damp[kr]);
-            }
-            const double sQ = __dmul_rn(g.sth, dQ);  // child of Q lands on R: +-sQ
-            const double sR = __dmul_rn(g.sth, dR);  // child of R lands on Q: -+sR
-            const double nQ = trunc(__dadd_rn(__dmul_rn(g.cth, dQ), with_sign(sR, !neg)));
-            const double nR = trunc(__dadd_rn(__dmul_rn(g.cth, dR), with_sign(sQ, neg)));
+            for (int j = 0; j < W; ++j) kr += __popcll((R.x(j) | R.z(j)) & g.supp[j]);
+            if (kq) dQ = __dmul_rn(dQ, g.damp[kq]);
+            if (own && kr) dR = __dmul_rn(dR, g.damp[kr]);
+          }
+          const double aQ = __dmul_rn(g.cth, dQ);
+          const double sQ = __dmul_rn(g.sth, dQ);  // child of Q lands on R: +-sQ
+          const double aR = __dmul_rn(g.cth, dR);
+          const double sR = __dmul_rn(g.sth, dR);  // child of R lands on Q: -+sR
+          const double mQ = __dadd_rn(aQ, with_sign(sR, !neg));
+          const double mR = __dadd_rn(aR, with_sign(sQ, neg));
+          const double nQ = trunc(own ? mQ : aQ);
+          t.coef[i] = nQ;
+          if (own) {
+            const double nR = trunc(mR);
             delta += (long long)!is_dead(nQ) - (long long)liveQ + (long long)!is_dead(nR) -
                      (long long)!is_dead(cR);
-            t.coef[i] = nQ;
             t.coef[jr] = nR;
-          }
-        } else if (jr == -1 && liveQ) {
-          const double dQ = (noise && kq) ? __dmul_rn(cQ, g.damp[kq]) : cQ;
-          const double nQ = trunc(__dmul_rn(g.cth, dQ));
-          delta -= is_dead(nQ);
-          t.coef[i] = nQ;
-          child = with_sign(__dmul_rn(g.sth, dQ), neg);
-          want = (g.wmax < 0 || weight(R) <= g.wmax) &&
-                 !(use_eps && (dbits(child) & kAbsMask) < eps_bits);
-        }
-      }
-    }
-    // stage the births of this warp in shared memory (one shared atomic per warp)
-    const unsigned ballot = __ballot_sync(kFull, want);
-    if (ballot) {
-      const int leader = __ffs(ballot) - 1;
-      unsigned b0 = 0;
-      if (lane == leader) b0 = atomicAdd(&sh.nstage, (unsigned)__popc(ballot));
-      b0 = __shfl_sync(kFull, b0, leader);
-      const unsigned pos = b0 + __popc(ballot & ((1u << lane) - 1u));
-      const bool staged = want && pos < (unsigned)GateStage<W>::kCap;
-      const bool direct = want && !staged;
-      Key<W> R;
-      if (want) {
-        const Key<W> Q = ld_key_cg<W>(t.keys, i);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-          R.x(j) = Q.x(j) ^ g.px[j];
-          R.z(j) = Q.z(j) ^ g.pz[j];
-        }
-      }
-      if (staged) {
-#pragma unroll
-        for (int j = 0; j < 2 * W; ++j) stage.key[pos][j] = R.w[j];
-        stage.coef[pos] = child;
-      }
-      const unsigned over = __ballot_sync(kFull, direct);
-      if (over) {  // staging area full: append straight away
-        const int ol = __ffs(over) - 1;
-        unsigned long long ob = 0;
-        if (lane == ol) ob = T0 + atomicAdd(cnt_slot, (unsigned long long)__popc(over));
-        ob = __shfl_sync(kFull, ob, ol);
-        if (direct) {
-          const uint64_t idx = ob + __popc(over & ((1u << lane) - 1u));
-          if (idx < t.cap) {
-            st_key<W>(t.keys, idx, R);
-            t.coef[idx] = child;
-            const uint64_t h = key_hash(R);
-            index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
           } else {
-            err |= kErrAppend;
+            delta -= is_dead(nQ);
+            child = with_sign(sQ, neg);
+            want = (g.wmax < 0 || weight(R) <= g.wmax) &&
+                   !(use_eps && (dbits(child) & kAbsMask) < eps_bits);
           }
         }
       }
-      delta += want;
+      // stage the births of this warp in shared memory (one shared atomic per warp)
+      const unsigned ballot = __ballot_sync(kFull, want);
+      if (ballot) {
+        const int leader = __ffs(ballot) - 1;
+        unsigned b0 = 0;
+        if (lane == leader) b0 = atomicAdd(&sh.nstage, (unsigned)__popc(ballot));
+        b0 = __shfl_sync(kFull, b0, leader);
+        const unsigned pos = b0 + __popc(ballot & lanes_below);
+        const bool staged = want && pos < (unsigned)GateStage<W>::kCap;
+        const bool direct = want && !staged;
+        if (staged) {
+#pragma unroll
+          for (int j = 0; j < 2 * W; ++j) stage.key[pos][j] = R.w[j];
+          stage.coef[pos] = child;
+        }
+        const unsigned over = __ballot_sync(kFull, direct);
+        if (over) {  // staging area full: append straight away
+          const int ol = __ffs(over) - 1;
+          unsigned long long ob = 0;
+          if (lane == ol) ob = T0 + atomicAdd(cnt_slot, (unsigned long long)__popc(over));
+          ob = __shfl_sync(kFull, ob, ol);
+          if (direct) {
+            const uint64_t idx = ob + __popc(over & lanes_below);
+            if (idx < t.cap) {
+              st_key<W>(t.keys, idx, R);
+              t.coef[idx] = child;
+              const uint64_t h = key_hash(R);
+              index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+            } else {
+              err |= kErrAppend;
+            }
+          }
+        }
+        delta += want;
+      }
     }
+    __syncwarp();  // the list is rewritten by the next tile
   }
   // the next kernel on the stream may now be scheduled (it waits for this grid)
   asm volatile("griddepcontrol.launch_dependents;");
@@ -245,6 +314,7 @@ template <int W>
 __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict__ tabp,
                                                       DevCtl* __restrict__ ctl, GateArgs g) {
   __shared__ GateStage<W> stage;
+  __shared__ GateList<W> list;
   __shared__ GateShared sh;
   const unsigned gid = g.gate_id;
   const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
@@ -277,7 +347,7 @@ __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict
     return;
   }
   __syncthreads();
-  gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, sh);
+  gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -322,10 +392,11 @@ __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_
 // a kernel boundary.  Gate ids, slots and the capacity stall are the same as
 // for gate_kernel, so chain_init / chain_finish serve both.
 template <int W>
-__global__ void __launch_bounds__(kBlock, (W == 1) ? 5 : ((W == 2) ? 3 : 2))
+__global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
     layer_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
                  const GateArgs* __restrict__ gates, unsigned n_gates) {
   __shared__ GateStage<W> stage;
+  __shared__ GateList<W> list;
   __shared__ GateShared sh;
   __shared__ GateArgs s_gate[2];  // current gate and the prefetched next one
   __shared__ int s_ok;
@@ -362,7 +433,7 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 5 : ((W == 2) ? 3 : 2))
       atomicAdd(&ctl->gates_done, 1ull);
     }
     __syncthreads();  // s_gate[buf] complete
-    gate_pass<W>(t, ctl, s_gate[buf], T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, sh);
+    gate_pass<W>(t, ctl, s_gate[buf], T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
     if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);  // overlaps the barrier wait
     if (!grid_sync(ctl, target, s_ok)) return;
     T0 += __ldcg(&ctl->cnt[slot]);
