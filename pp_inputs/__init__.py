@@ -289,12 +289,28 @@ def config2_all_to_all(n: int = 64, dt: float = 0.02, steps: int = 10, p: float 
 
 
 def xxz_all_to_all(n: int, delta_t: float, steps: int, J: float = 1.0, Delta: float = -1.8,
-                   eps: float = 0.0, symmetry: int = 0, gamma: float = 0.0) -> Workload:
-    """Eq. hamXXZ with alpha = 0: h_ij = -J (XX + YY + (Delta+1) ZZ); S^2; |+>^n."""
+                   eps: float = 0.0, symmetry: int = 0, gamma: float = 0.0,
+                   split: bool = False) -> Workload:
+    """Eq. hamXXZ with alpha = 0: h_ij = -J (XX + YY + (Delta+1) ZZ); S^2; |+>^n.
+
+    split=False: one layer per Trotter step, pairs (i, j) in lexicographic
+    order with XX, YY, ZZ inner.  split=True: each step is three layers (all
+    XX over the pairs, then all YY, then all ZZ).  Each of those is a set of
+    commuting gates invariant under S_n, so a runner that merges at layer
+    boundaries merges after every sublayer.  The per-step damping gamma is
+    only defined for split=False.
+    """
     th_xy = -2.0 * J * delta_t
     th_zz = -2.0 * J * (Delta + 1.0) * delta_t
     layer = heisenberg_layer(n, th_xy, th_xy, th_zz)
-    return Workload("xxz_a2a_n%d_x%d" % (n, steps), Circuit(n, [list(layer) for _ in range(steps)]),
+    if not split:
+        layers = [list(layer) for _ in range(steps)]
+    else:
+        if gamma > 0:
+            raise ValueError("per-step damping is defined for unsplit steps only")
+        subs = [[g for g in layer if set(g[0].replace("I", "")) == {p}] for p in "XYZ"]
+        layers = [list(sub) for _ in range(steps) for sub in subs]
+    return Workload("xxz_a2a_n%d_x%d%s" % (n, steps, "_split" if split else ""), Circuit(n, layers),
                     total_spin_squared(n), plus_state(n), eps=eps,
                     noise_p=gamma, noise_mode=2 if gamma > 0 else 0, symmetry=symmetry)
 
