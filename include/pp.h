@@ -142,9 +142,12 @@ pp_status pp_destroy(pp_ctx* ctx);
  * from the last (l = L) to the first (l = 1).
  * Errors: PP_ERR_ARG; PP_ERR_SYMMETRY when check_symmetry is set and the gate
  * multiset (with angles) is not mapped onto itself by the group generators;
- * PP_ERR_CAPACITY when the table would exceed the budget -- the context then
- * holds the state after the last completed gate and pp_stats reports it;
- * PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_INTERNAL. */
+ * PP_ERR_CAPACITY when the table would exceed mem_budget_bytes -- the context
+ * is then back at its state before the call (a dense copy of the table,
+ * counted against the budget, is taken at the start of every call on a
+ * context with a budget), so the caller may raise the budget with
+ * pp_set_budget and call again; PP_ERR_OOM, PP_ERR_CUDA, PP_ERR_INTERNAL
+ * (after these the context holds a partly applied layer). */
 pp_status pp_apply_layer(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const double* theta,
                          int symmetric_boundary);
 

@@ -871,6 +871,134 @@ pp_status ensure_merged(pp_ctx* c) {
   return merge_active(c, PP_SYM_NONE);
 }
 
+// Dense copy of the stored entries [0, n) of the active table (keys and
+// coefficients or rows; no index).
+pp_status take_snapshot(pp_ctx* c, Buf& s, uint64_t n) {
+  s = Buf();
+  if (n == 0) return PP_OK;
+  const size_t need = (size_t)n * (16 * c->W + c->row_bytes());
+  if (c->bytes + need > c->cfg.mem_budget_bytes)
+    return fail(PP_ERR_CAPACITY, "no room in the memory budget for the copy that lets a layer be undone");
+  const Buf& a = c->buf[c->active];
+  PP_TRY(dmalloc(c, (void**)&s.keys, (size_t)n * 16 * c->W));
+  PP_CUDA(cudaMemcpyAsync(s.keys, a.keys, (size_t)n * 16 * c->W, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->batched) {
+    PP_TRY(dmalloc(c, &s.rows, (size_t)n * c->B * c->esize));
+    PP_TRY(dmalloc(c, (void**)&s.alive, (size_t)n));
+    PP_CUDA(cudaMemcpyAsync(s.rows, a.rows, (size_t)n * c->B * c->esize, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    PP_CUDA(cudaMemcpyAsync(s.alive, a.alive, (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    PP_TRY(dmalloc(c, (void**)&s.coef, (size_t)n * 8));
+    PP_CUDA(cudaMemcpyAsync(s.coef, a.coef, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  s.cap = n;
+  return PP_OK;
+}
+
+void free_snapshot(pp_ctx* c, Buf& s, uint64_t n) {
+  dfree(c, s.keys, (size_t)n * 16 * c->W);
+  dfree(c, s.coef, (size_t)n * 8);
+  dfree(c, s.rows, (size_t)n * c->B * c->esize);
+  dfree(c, s.alive, (size_t)n);
+  s = Buf();
+}
+
+// Rebuild the active table (entries and index) from a snapshot of n entries.
+// The active table's capacity never drops below what it held at the
+// snapshot, so the entries fit.
+pp_status restore_snapshot(pp_ctx* c, const Buf& s, uint64_t n) {
+  Buf& d = c->buf[c->active];
+  if (d.cap < n) return fail(PP_ERR_INTERNAL, "table shrank below its size before the layer");
+  PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
+  PP_TRY(ctl_prepare_insert(c, 0));
+  if (n > 0) {
+    DevTable src = desc_of(c, s);
+    src.index = nullptr;
+    src.imask = 0;
+    if (c->batched) {
+      PP_CUDA(launch_compact_batched(c->W, grid_for(c, n, 4), c->stream, src, n, desc_of(c, d), 1,
+                                     0.0, -1, c->d_ctl));
+    } else {
+      PP_CUDA(launch_compact(c->W, grid_for(c, n, 4), c->stream, src, n, desc_of(c, d), 1,
+                             c->cfg.coeff_eps, 0.0, -1, c->d_ctl));
+    }
+    c->launches += 1;
+  }
+  PP_TRY(ctl_commit(c));
+  PP_TRY(activate(c, c->active));
+  c->merged = true;
+  return PP_OK;
+}
+
+// Everything pp_apply_layer does after the entry merge: damping, room, the
+// gate launches (with the capacity-stall loop) and the boundary merge.
+pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::vector<int>& src_t,
+                           const double* theta, int symmetric_boundary) {
+  if (c->cfg.noise_mode == PP_NOISE_PER_LAYER && c->n_terms > 0) {
+    PP_CUDA(launch_damp_layer(c->W, grid_for(c, c->n_terms, 4), c->stream,
+                              desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
+    c->launches += 1;
+  }
+  PP_TRY(make_room(c));
+  const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
+  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0 && !c->batched;
+  if (c->batched && !args.empty()) PP_TRY(batched_columns(c, args, src_t, theta));
+  int grid_b = 1;
+  if (layered) {
+    // persistent: one string per thread per pass, never more blocks than can
+    // be co-resident (the grid barrier needs all of them)
+    const uint64_t want = (est + kBlock - 1) / kBlock;
+    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
+  } else {
+    // a power of two so that captured graphs are reused
+    while ((uint64_t)grid_b * kBlock < est) grid_b <<= 1;
+    grid_b = std::min(grid_b, c->sms * c->gate_bps);
+  }
+  const GateArgs* d_args = nullptr;
+  if (layered && !args.empty()) PP_TRY(device_args(c, args, &d_args));
+  if (!args.empty()) {
+    unsigned first = 0;
+    for (;;) {
+      PP_CUDA(launch_chain_init(c->stream, c->d_ctl, first));
+      if (layered) {
+        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[0], c->stream));
+        PP_CUDA(launch_layer(c->W, grid_b, c->stream, c->d_desc + 2, c->d_ctl, d_args,
+                             (unsigned)args.size()));
+        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[1], c->stream));
+        c->launches += 1;
+      } else {
+        PP_TRY(launch_layer_gates(c, args, grid_b));
+      }
+      PP_CUDA(launch_chain_finish(c->stream, c->d_ctl, (unsigned)args.size()));
+      c->launches += 2;
+      PP_TRY(read_ctl(c));
+      PP_TRY(check_device_error(c));
+      const unsigned end = c->h_ctl->stall ? c->h_ctl->stall - 1u : (unsigned)args.size();
+      if (layered) {
+        if (c->cfg.profile_kernels && end > first) {
+          float ms = 0.f;
+          PP_CUDA(cudaEventElapsedTime(&ms, c->ev_layer[0], c->ev_layer[1]));
+          c->gate_ms += ms;
+          c->gates_timed++;
+        }
+      } else {
+        PP_TRY(collect_gate_times(c, first, end));
+      }
+      c->n_terms = c->h_ctl->n_terms;
+      c->n_live = c->h_ctl->n_live;
+      if (!c->h_ctl->stall) break;
+      // gate `end` found too little room: compact and grow, then resume there
+      PP_TRY(make_room(c));
+      first = end;
+    }
+  }
+  if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE) {
+    PP_TRY(merge_active(c, c->cfg.symmetry));
+  }
+  return PP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -963,68 +1091,30 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
     }
   }
   PP_TRY(ensure_merged(c));
-  if (c->cfg.noise_mode == PP_NOISE_PER_LAYER && c->n_terms > 0) {
-    PP_CUDA(launch_damp_layer(c->W, grid_for(c, c->n_terms, 4), c->stream,
-                              desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
-    c->launches += 1;
-  }
-  PP_TRY(make_room(c));
-  const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
-  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0 && !c->batched;
-  if (c->batched && !args.empty()) PP_TRY(batched_columns(c, args, src_t, theta));
-  int grid_b = 1;
-  if (layered) {
-    // persistent: one string per thread per pass, never more blocks than can
-    // be co-resident (the grid barrier needs all of them)
-    const uint64_t want = (est + kBlock - 1) / kBlock;
-    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
-  } else {
-    // a power of two so that captured graphs are reused
-    while ((uint64_t)grid_b * kBlock < est) grid_b <<= 1;
-    grid_b = std::min(grid_b, c->sms * c->gate_bps);
-  }
-  const GateArgs* d_args = nullptr;
-  if (layered && !args.empty()) PP_TRY(device_args(c, args, &d_args));
-  if (!args.empty()) {
-    unsigned first = 0;
-    for (;;) {
-      PP_CUDA(launch_chain_init(c->stream, c->d_ctl, first));
-      if (layered) {
-        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[0], c->stream));
-        PP_CUDA(launch_layer(c->W, grid_b, c->stream, c->d_desc + 2, c->d_ctl, d_args,
-                             (unsigned)args.size()));
-        if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[1], c->stream));
-        c->launches += 1;
-      } else {
-        PP_TRY(launch_layer_gates(c, args, grid_b));
-      }
-      PP_CUDA(launch_chain_finish(c->stream, c->d_ctl, (unsigned)args.size()));
-      c->launches += 2;
-      PP_TRY(read_ctl(c));
-      PP_TRY(check_device_error(c));
-      const unsigned end = c->h_ctl->stall ? c->h_ctl->stall - 1u : (unsigned)args.size();
-      if (layered) {
-        if (c->cfg.profile_kernels && end > first) {
-          float ms = 0.f;
-          PP_CUDA(cudaEventElapsedTime(&ms, c->ev_layer[0], c->ev_layer[1]));
-          c->gate_ms += ms;
-          c->gates_timed++;
-        }
-      } else {
-        PP_TRY(collect_gate_times(c, first, end));
-      }
-      c->n_terms = c->h_ctl->n_terms;
-      c->n_live = c->h_ctl->n_live;
-      if (!c->h_ctl->stall) break;
-      // gate `end` found too little room: compact and grow, then resume there
-      PP_TRY(make_room(c));
-      first = end;
+  // With a memory budget a layer may stop with PP_ERR_CAPACITY part way
+  // through; the table is then put back as it was before the call, from a
+  // dense copy taken here (counted against the budget).
+  const bool keep_state = c->cfg.mem_budget_bytes > 0;
+  Buf snap;
+  const uint64_t snap_n = c->n_terms;
+  if (keep_state) {
+    const pp_status ts = take_snapshot(c, snap, snap_n);
+    if (ts != PP_OK) {
+      free_snapshot(c, snap, snap_n);
+      return ts;
     }
   }
-  if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE) {
-    PP_TRY(merge_active(c, c->cfg.symmetry));
+  pp_status st = apply_layer_core(c, args, src_t, theta, symmetric_boundary);
+  if (st == PP_ERR_CAPACITY && keep_state) {
+    const std::string msg = g_last_error;
+    const pp_status rs = restore_snapshot(c, snap, snap_n);
+    free_snapshot(c, snap, snap_n);
+    if (rs != PP_OK) return rs;
+    g_last_error = msg + " (context restored to its state before the call)";
+    return PP_ERR_CAPACITY;
   }
-  return PP_OK;
+  if (keep_state) free_snapshot(c, snap, snap_n);
+  return st;
 }
 
 pp_status pp_canonicalize(pp_ctx* c) {

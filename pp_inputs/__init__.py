@@ -291,7 +291,7 @@ def config2_all_to_all(n: int = 64, dt: float = 0.02, steps: int = 10, p: float 
 def xxz_all_to_all(n: int, delta_t: float, steps: int, J: float = 1.0, Delta: float = -1.8,
                    eps: float = 0.0, symmetry: int = 0, gamma: float = 0.0,
                    split: bool = False) -> Workload:
-    """Eq. hamXXZ with alpha = 0: h_ij = -J (XX + YY + (Delta+1) ZZ); S^2; |+>^n.
+    """Eq. hamXXZ with alpha = 0: h_ij = -J (XX + YY + (Delta+1) ZZ); S^2 / S_0^2; |+>^n.
 
     split=False: one layer per Trotter step, pairs (i, j) in lexicographic
     order with XX, YY, ZZ inner.  split=True: each step is three layers (all
@@ -310,8 +310,11 @@ def xxz_all_to_all(n: int, delta_t: float, steps: int, J: float = 1.0, Delta: fl
             raise ValueError("per-step damping is defined for unsplit steps only")
         subs = [[g for g in layer if set(g[0].replace("I", "")) == {p}] for p in "XYZ"]
         layers = [list(sub) for _ in range(steps) for sub in subs]
+    obs = total_spin_squared(n)
+    s0 = (n / 2.0) * (n / 2.0 + 1.0)  # <+|S^2|+>: the figure's normalisation S_0^2
+    obs = Observable(n, [(s, c / s0) for s, c in obs.terms])
     return Workload("xxz_a2a_n%d_x%d%s" % (n, steps, "_split" if split else ""), Circuit(n, layers),
-                    total_spin_squared(n), plus_state(n), eps=eps,
+                    obs, plus_state(n), eps=eps,
                     noise_p=gamma, noise_mode=2 if gamma > 0 else 0, symmetry=symmetry)
 
 
