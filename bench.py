@@ -214,14 +214,9 @@ def bench_ours(args):
                 e2e_ms += ev[0].elapsed_time(ev[2])
     pupd = upd
 
-    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = float(t[0]), float(t[1])
-    upd_per_rank = upd / args.steps
-    total_upd = upd_per_rank * world * args.steps
-    value = total_upd / (ms_max / 1e3)
-    e2e_value = total_upd / (e2e_max / 1e3) if e2e_max > 0 else None
+    value, e2e_value, ms_max, e2e_max, total_upd = replica_throughput(dist, ms_total, e2e_ms, upd,
+                                                                      dev)
+    upd_per_rank = upd / args.steps  # one job's updates (the same on every rank)
     hbm, peak_kind = peaks()
     per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
     bytes_alg = KEY_BYTES * pupd + per_ac * ac
@@ -420,6 +415,23 @@ def bench_serving(args):
             "offered_load_wall_s": float(specs[-1][0]),
             "max_abs_diff_vs_sequential": err}
     print(json.dumps(line), flush=True)
+
+
+def replica_throughput(dist, ms_total, e2e_ms, upd, device):
+    """Whole-job rate of N independent replicas (one per rank): the updates
+    of all ranks over the slowest rank's time, for the device-timed and the
+    end-to-end regions.  dist is torch.distributed (or None for one rank).
+    Returns (value, e2e_value, ms_max, e2e_max, total_updates)."""
+    import torch
+    t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([upd], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, e2e_max, total = float(t[0]), float(t[1]), float(u[0])
+    value = total / (ms_max / 1e3)
+    e2e_value = total / (e2e_max / 1e3) if e2e_max > 0 else None
+    return value, e2e_value, ms_max, e2e_max, total
 
 
 def bench_reference(args):
