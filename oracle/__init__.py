@@ -97,6 +97,16 @@ def _f64(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+# Group codes shared with the library's C ABI (plain integers): 1 = Z_n,
+# 2 = S_n, 3 = D_n (rotations and reflections of a ring), and
+# torus_group(Lx) = translations of an Lx x (n / Lx) torus, qubit q = x + Lx y.
+ZN, SN, DN = 1, 2, 3
+
+
+def torus_group(lx: int) -> int:
+    return 4 | (lx << 8)
+
+
 class OracleState:
     """Heisenberg-picture operator O = sum_s c_s s held by the C++ oracle."""
 

@@ -121,9 +121,70 @@ std::string canonical_sn(const std::string& s) {
   return r;
 }
 
+// Group codes: 1 = Z_n, 2 = S_n, 3 = D_n (the n rotations and n reflections of
+// a ring, Sec. "Symmetry" / Appendix B: dihedral symmetry), 4 | (Lx << 8) =
+// translations of an Lx x Ly torus with qubit q = x + Lx y (the 2D
+// translations used for the XXZ figure).
+int group_kind(int group) { return group & 0xFF; }
+int group_lx(int group) { return group >> 8; }
+
+// Every element of D_n or of the torus translations as a map of sites: the
+// letter of site q moves to site m[q].
+std::vector<std::vector<int>> group_elements(int group, int n) {
+  std::vector<std::vector<int>> out;
+  if (group_kind(group) == 3) {
+    for (int j = 0; j < n; ++j) {
+      std::vector<int> rot(n), ref(n);
+      for (int q = 0; q < n; ++q) {
+        rot[q] = (q + j) % n;
+        ref[q] = (n - 1 - q + j) % n;
+      }
+      out.push_back(rot);
+      out.push_back(ref);
+    }
+  } else if (group_kind(group) == 4) {
+    const int lx = group_lx(group), ly = n / lx;
+    for (int dy = 0; dy < ly; ++dy)
+      for (int dx = 0; dx < lx; ++dx) {
+        std::vector<int> m(n);
+        for (int q = 0; q < n; ++q) {
+          const int x = q % lx, y = q / lx;
+          m[q] = (x + dx) % lx + lx * ((y + dy) % ly);
+        }
+        out.push_back(m);
+      }
+  }
+  return out;
+}
+
+const std::vector<std::vector<int>>& cached_elements(int group, int n) {
+  static std::map<std::pair<int, int>, std::vector<std::vector<int>>> cache;
+  auto key = std::make_pair(group, n);
+  auto it = cache.find(key);
+  if (it == cache.end()) it = cache.emplace(key, group_elements(group, n)).first;
+  return it->second;
+}
+
+std::string apply_map(const std::string& s, const std::vector<int>& m) {
+  std::string r(s.size(), '\0');
+  for (size_t q = 0; q < s.size(); ++q) r[m[q]] = s[q];
+  return r;
+}
+
+// Lowest integer representative by enumerating every group element.
+std::string canonical_by_elements(const std::string& s, int group) {
+  std::string best = s;
+  for (const auto& m : cached_elements(group, (int)s.size())) {
+    std::string t = apply_map(s, m);
+    if (int_less(t, best)) best = t;
+  }
+  return best;
+}
+
 std::string canonical(const std::string& s, int group) {
   if (group == 1) return canonical_zn(s);
   if (group == 2) return canonical_sn(s);
+  if (group_kind(group) == 3 || group_kind(group) == 4) return canonical_by_elements(s, group);
   return s;
 }
 
@@ -271,6 +332,12 @@ double sym_overlap(State* st, const std::string& s, const double* bloch, int gro
     }
     int S = st->n + 1;
     return st->sn_table[((size_t)nx * S + ny) * S + nz];
+  }
+  if (group_kind(group) == 3 || group_kind(group) == 4) {
+    const auto& els = cached_elements(group, st->n);
+    double acc = 0.0;
+    for (const auto& m : els) acc += product_overlap(apply_map(s, m), bloch);
+    return acc / (double)els.size();
   }
   return product_overlap(s, bloch);
 }

@@ -214,6 +214,24 @@ def ring_layer(n: int, theta_j: float, theta_x: float, theta_z: float):
     return gates
 
 
+def torus_layer(lx: int, ly: int, theta_j: float, theta_x: float, theta_z: float):
+    """One Trotter step on an lx x ly torus (qubit q = x + lx y): RZZ on every
+    horizontal bond, then on every vertical bond, then RX and RZ on every
+    site.  Each group of gates commutes and is mapped onto itself by the
+    lattice translations."""
+    n = lx * ly
+    gates = []
+    for y in range(ly):
+        for x in range(lx):
+            gates.append((pauli(n, {x + lx * y: "Z", (x + 1) % lx + lx * y: "Z"}), theta_j))
+    for y in range(ly):
+        for x in range(lx):
+            gates.append((pauli(n, {x + lx * y: "Z", x + lx * ((y + 1) % ly): "Z"}), theta_j))
+    gates += [(pauli(n, {q: "X"}), theta_x) for q in range(n)]
+    gates += [(pauli(n, {q: "Z"}), theta_z) for q in range(n)]
+    return gates
+
+
 def tilted_ising_layer(n: int, delta: float, hx: float = 1.4, hz: float = 0.9045):
     """Trotter layer of H = -sum ZZ - hz sum Z - hx sum X on a ring.
 
@@ -316,6 +334,16 @@ def xxz_all_to_all(n: int, delta_t: float, steps: int, J: float = 1.0, Delta: fl
     return Workload("xxz_a2a_n%d_x%d%s" % (n, steps, "_split" if split else ""), Circuit(n, layers),
                     obs, plus_state(n), eps=eps,
                     noise_p=gamma, noise_mode=2 if gamma > 0 else 0, symmetry=symmetry)
+
+
+def torus_ising(lx: int, ly: int, steps: int, theta_j: float = 0.4, theta_x: float = 0.6,
+                theta_z: float = 0.3, eps: float = 0.0, max_weight: int = -1,
+                symmetry: int = 0) -> Workload:
+    """The ring workload's gate set on an lx x ly torus: (1/n) sum Z_i, |0...0>."""
+    n = lx * ly
+    layer = torus_layer(lx, ly, theta_j, theta_x, theta_z)
+    return Workload("torus_%dx%d_x%d" % (lx, ly, steps), Circuit(n, [list(layer) for _ in range(steps)]),
+                    mean_z(n), zero_state(n), eps=eps, max_weight=max_weight, symmetry=symmetry)
 
 
 def batched_ring_angles(n_sets: int = 256, seed: int = 0) -> np.ndarray:
