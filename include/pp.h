@@ -52,7 +52,23 @@ typedef enum {
   PP_ERR_INTERNAL = 10  /* device-side consistency check failed (hash probe bound) */
 } pp_status;
 
-typedef enum { PP_SYM_NONE = 0, PP_SYM_ZN = 1, PP_SYM_SN = 2 } pp_symmetry;
+/* Symmetry groups (Sec. "Symmetry" and Appendix B of the paper).
+ *  PP_SYM_ZN     translations of a ring of n qubits (Algorithm 2);
+ *  PP_SYM_SN     all permutations of the n qubits (Algorithm 3);
+ *  PP_SYM_DN     translations and reflections of a ring (dihedral group);
+ *  PP_SYM_TORUS  translations of an Lx x Ly torus, qubit q = x + Lx y, used as
+ *                PP_SYM_TORUS_LX(Lx) = 4 | (Lx << 8); Lx must divide n.
+ * Every representative is the lowest-integer member of its orbit
+ * (I=0, X=1, Y=2, Z=3, qubit q the digit of weight 4^q).  A `symmetry`
+ * argument anywhere in this API takes one of these codes. */
+typedef enum {
+  PP_SYM_NONE = 0,
+  PP_SYM_ZN = 1,
+  PP_SYM_SN = 2,
+  PP_SYM_DN = 3,
+  PP_SYM_TORUS = 4
+} pp_symmetry;
+#define PP_SYM_TORUS_LX(lx) ((int)PP_SYM_TORUS | ((int)(lx) << 8))
 typedef enum { PP_COEF_F64 = 0, PP_COEF_F32 = 1 } pp_coef_type;
 typedef enum { PP_NOISE_NONE = 0, PP_NOISE_PER_GATE = 1, PP_NOISE_PER_LAYER = 2 } pp_noise_mode;
 

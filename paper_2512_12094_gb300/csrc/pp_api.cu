@@ -388,17 +388,47 @@ void permute_string(const uint64_t* x, const uint64_t* z, int n, int W, const st
   }
 }
 
+// Group codes: kind in the low byte (pp_symmetry), torus width above it.
+int group_kind(int code) { return code & 0xFF; }
+int group_lx(int code) { return code >> 8; }
+
+bool valid_group(int code, int n) {
+  const int kind = group_kind(code), lx = group_lx(code);
+  if (code < 0 || kind > PP_SYM_TORUS) return false;
+  if (kind == PP_SYM_TORUS) return lx >= 1 && lx <= n && n % lx == 0;
+  return lx == 0;
+}
+
+// Generators of the group as site maps (the letter of q moves to to[q]).
 std::vector<std::vector<int>> generators(int group, int n) {
   std::vector<std::vector<int>> gens;
-  if (n < 2 || group == PP_SYM_NONE) return gens;
+  const int kind = group_kind(group);
+  if (n < 2 || kind == PP_SYM_NONE) return gens;
+  if (kind == PP_SYM_TORUS) {
+    const int lx = group_lx(group), ly = n / lx;
+    std::vector<int> sx(n), sy(n);
+    for (int q = 0; q < n; ++q) {
+      const int x = q % lx, y = q / lx;
+      sx[q] = (x + 1) % lx + lx * y;
+      sy[q] = x + lx * ((y + 1) % ly);
+    }
+    gens.push_back(sx);
+    gens.push_back(sy);
+    return gens;
+  }
   std::vector<int> shift(n);
   for (int q = 0; q < n; ++q) shift[q] = (q + n - 1) % n;  // T: qubit q -> q-1
   gens.push_back(shift);
-  if (group == PP_SYM_SN) {
+  if (kind == PP_SYM_SN) {
     std::vector<int> swap01(n);
     for (int q = 0; q < n; ++q) swap01[q] = q;
     std::swap(swap01[0], swap01[1]);
     gens.push_back(swap01);
+  }
+  if (kind == PP_SYM_DN) {
+    std::vector<int> refl(n);
+    for (int q = 0; q < n; ++q) refl[q] = n - 1 - q;
+    gens.push_back(refl);
   }
   return gens;
 }
@@ -445,8 +475,8 @@ pp_status validate_config(const pp_config* cfg) {
   if (!cfg) return fail(PP_ERR_ARG, "config is null");
   if (cfg->n_qubits < 1 || cfg->n_qubits > 64 * kMaxW)
     return fail(PP_ERR_ARG, "n_qubits must be in 1..256");
-  if (cfg->symmetry < PP_SYM_NONE || cfg->symmetry > PP_SYM_SN)
-    return fail(PP_ERR_ARG, "unknown symmetry");
+  if (!valid_group(cfg->symmetry, cfg->n_qubits))
+    return fail(PP_ERR_ARG, "unknown symmetry, or a torus width that does not divide n_qubits");
   if (cfg->batch < 1 || cfg->batch > 512) return fail(PP_ERR_ARG, "batch must be in 1..512");
   if (cfg->coef_type != PP_COEF_F64 && cfg->coef_type != PP_COEF_F32)
     return fail(PP_ERR_ARG, "unknown coef_type");
@@ -1150,9 +1180,10 @@ pp_status pp_expect(pp_ctx* c, const double* bloch, double* out) {
   OverlapArgs a;
   memset(&a, 0, sizeof(a));
   a.n = n;
-  a.group = c->cfg.symmetry;
+  a.group = group_kind(c->cfg.symmetry);
+  a.lx = group_lx(c->cfg.symmetry);
   if (a.group != PP_SYM_NONE) {
-    if (bloch_invariant(a.group, n, bloch)) {
+    if (bloch_invariant(c->cfg.symmetry, n, bloch)) {
       a.group = PP_SYM_NONE;  // Eq. 2: orbit members have equal overlaps
     } else if (!c->obs_invariant) {
       return fail(PP_ERR_SYMMETRY, "neither the state nor the observable is invariant");
@@ -1305,7 +1336,7 @@ const char* pp_last_error(void) { return g_last_error.c_str(); }
 pp_status pp_canonical_keys(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
                             uint64_t* keys_out, void* stream) {
   if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
-  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (!valid_group(symmetry, n_qubits)) return fail(PP_ERR_ARG, "bad symmetry");
   if (m < 0 || (m > 0 && (!keys_in || !keys_out))) return fail(PP_ERR_ARG, "bad arrays");
   if (m == 0) return PP_OK;
   const int W = (n_qubits + 63) / 64;
@@ -1320,7 +1351,7 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
                          const double* coef_in, uint64_t* keys_out, double* coef_out,
                          int64_t* m_out, void* stream) {
   if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
-  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (!valid_group(symmetry, n_qubits)) return fail(PP_ERR_ARG, "bad symmetry");
   if (!m_out || m < 0 || (m > 0 && (!keys_in || !coef_in || !keys_out || !coef_out)))
     return fail(PP_ERR_ARG, "bad arrays");
   if ((uint64_t)m >= (1ull << 31)) return fail(PP_ERR_ARG, "too many terms");
@@ -1365,7 +1396,7 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* keys,
                          const double* coef, const double* bloch, double* out, void* stream) {
   if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
-  if (symmetry < 0 || symmetry > 2) return fail(PP_ERR_ARG, "bad symmetry");
+  if (!valid_group(symmetry, n_qubits)) return fail(PP_ERR_ARG, "bad symmetry");
   if (m < 0 || !out || !bloch || (m > 0 && (!keys || !coef))) return fail(PP_ERR_ARG, "bad arrays");
   cudaStream_t s = (cudaStream_t)stream;
   const int W = (n_qubits + 63) / 64;
@@ -1383,7 +1414,8 @@ pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* 
   OverlapArgs a;
   memset(&a, 0, sizeof(a));
   a.n = n_qubits;
-  a.group = symmetry;
+  a.group = group_kind(symmetry);
+  a.lx = group_lx(symmetry);
   a.basis = 0;
   a.bloch = bloch;
   a.sn_table = sn;
@@ -1398,3 +1430,5 @@ pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 }
 
 }  // extern "C"
+
+bool ppk::valid_group_code(int code, int n) { return valid_group(code, n); }

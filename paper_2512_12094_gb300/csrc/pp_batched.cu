@@ -263,7 +263,7 @@ template <int W, int G, typename S>
 __global__ void __launch_bounds__(kBlock)
     merge_batched_kernel(const uint64_t* __restrict__ src_keys, const S* __restrict__ src_rows,
                          const unsigned char* __restrict__ src_alive, uint64_t count, int wmax,
-                         int n, DevTable dst, double* acc, DevCtl* ctl) {
+                         int n, int lx, DevTable dst, double* acc, DevCtl* ctl) {
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31;
   const int B = dst.B;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kBlock)
     if (lane == 0 && (!src_alive || src_alive[e])) {
       Key<W> K = ld_key<W>(src_keys, e);
       if (wmax < 0 || weight(K) <= wmax) {
-        canon<W, G>(K, n);
+        canon<W, G>(K, n, lx);
         const uint64_t h = key_hash(K);
         const uint32_t tag = tag_of(h);
         uint64_t pos = h & dst.imask;
@@ -441,8 +441,10 @@ __global__ void __launch_bounds__(kBlock)
     double ov = 0.0;
     if (lane == 0) {
       const Key<W> k = ld_key<W>(t.keys, e);
-      ov = a.group == 1 ? overlap_zn<W>(k, a) : (a.group == 2 ? overlap_sn<W>(k, a)
-                                                                 : overlap_plain<W>(k, a));
+      ov = a.group == 1   ? overlap_zn<W>(k, a)
+           : a.group == 2 ? overlap_sn<W>(k, a)
+           : (a.group == 3 || a.group == 4) ? overlap_group<W>(k, a)
+                                             : overlap_plain<W>(k, a);
     }
     ov = __shfl_sync(kAll, ov, 0);
     if (ov != 0.0)
@@ -510,16 +512,16 @@ cudaError_t launch_gate_batched(int W, int f32, int grid, cudaStream_t s, const 
 }
 
 template <int W, int G>
-static cudaError_t merge_b_g(int n, int wmax, int src_f32, int grid, cudaStream_t s,
+static cudaError_t merge_b_g(int n, int lx, int wmax, int src_f32, int grid, cudaStream_t s,
                              const uint64_t* src_keys, const void* src_rows,
                              const unsigned char* src_alive, uint64_t count, DevTable dst,
                              double* acc, DevCtl* ctl) {
   if (src_f32)
     merge_batched_kernel<W, G, float><<<grid, kBlock, 0, s>>>(
-        src_keys, static_cast<const float*>(src_rows), src_alive, count, wmax, n, dst, acc, ctl);
+        src_keys, static_cast<const float*>(src_rows), src_alive, count, wmax, n, lx, dst, acc, ctl);
   else
     merge_batched_kernel<W, G, double><<<grid, kBlock, 0, s>>>(
-        src_keys, static_cast<const double*>(src_rows), src_alive, count, wmax, n, dst, acc, ctl);
+        src_keys, static_cast<const double*>(src_rows), src_alive, count, wmax, n, lx, dst, acc, ctl);
   return cudaGetLastError();
 }
 
@@ -527,19 +529,20 @@ cudaError_t launch_merge_batched(int W, int group, int n, int wmax, int src_f32,
                                  cudaStream_t s, const uint64_t* src_keys, const void* src_rows,
                                  const unsigned char* src_alive, uint64_t count, DevTable dst,
                                  double* acc, DevCtl* ctl) {
-  switch (group) {
-    case 0:
-      PPB_W(W, return (merge_b_g<WW, 0>(n, wmax, src_f32, grid, s, src_keys, src_rows, src_alive,
-                                        count, dst, acc, ctl)));
-    case 1:
-      PPB_W(W, return (merge_b_g<WW, 1>(n, wmax, src_f32, grid, s, src_keys, src_rows, src_alive,
-                                        count, dst, acc, ctl)));
-    case 2:
-      PPB_W(W, return (merge_b_g<WW, 2>(n, wmax, src_f32, grid, s, src_keys, src_rows, src_alive,
-                                        count, dst, acc, ctl)));
+  const int lx = group >> 8;  // group code: kind | (torus width << 8)
+#define PPB_G(GG)                                                                          \
+  PPB_W(W, return (merge_b_g<WW, GG>(n, lx, wmax, src_f32, grid, s, src_keys, src_rows,   \
+                                     src_alive, count, dst, acc, ctl)))
+  switch (group & 0xFF) {
+    case 0: PPB_G(0);
+    case 1: PPB_G(1);
+    case 2: PPB_G(2);
+    case 3: PPB_G(3);
+    case 4: PPB_G(4);
     default:
       return cudaErrorInvalidValue;
   }
+#undef PPB_G
 }
 
 cudaError_t launch_finalize_batched(int grid, cudaStream_t s, DevTable dst, const double* acc,

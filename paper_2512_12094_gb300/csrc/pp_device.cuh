@@ -301,16 +301,159 @@ __device__ __forceinline__ void canon_sn(Key<W>& k) {
   }
 }
 
-template <int W, int G>
-__device__ __forceinline__ void canon(Key<W>& k, int n) {
-  if constexpr (G == 1) {
-    if constexpr (W == 1) {
-      canon_zn_w1(k, n);
-    } else {
-      canon_zn_generic<W>(k, n);
+template <int W>
+__device__ __forceinline__ void canon_zn(Key<W>& k, int n) {
+  if constexpr (W == 1) {
+    canon_zn_w1(k, n);
+  } else {
+    canon_zn_generic<W>(k, n);
+  }
+}
+
+// Digit-integer order of Definition "Lowest integer representation": the
+// first differing digit from the most significant qubit decides.
+template <int W>
+__device__ __forceinline__ bool key_less(const Key<W>& a, const Key<W>& b) {
+#pragma unroll
+  for (int j = W - 1; j >= 0; --j) {
+    const uint64_t la = a.x(j) ^ a.z(j), lb = b.x(j) ^ b.z(j);  // low digit bits
+    const uint64_t diff = (a.z(j) ^ b.z(j)) | (la ^ lb);
+    if (diff) {
+      const int q = 63 - __clzll((long long)diff);
+      const int va = (int)(((a.z(j) >> q) & 1ull) << 1 | ((la >> q) & 1ull));
+      const int vb = (int)(((b.z(j) >> q) & 1ull) << 1 | ((lb >> q) & 1ull));
+      return va < vb;
     }
+  }
+  return false;
+}
+
+// Reflection of the ring: the letter of qubit q moves to qubit n-1-q.
+template <int W>
+__device__ __forceinline__ Key<W> reflect_key(const Key<W>& k, int n) {
+  Key<W> r;
+  if constexpr (W == 1) {
+    r.x(0) = __brevll(k.x(0)) >> (64 - n);
+    r.z(0) = __brevll(k.z(0)) >> (64 - n);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
+    for (int q = 0; q < n; ++q) {
+      const int t = n - 1 - q;
+      r.x(t >> 6) |= ((k.x(q >> 6) >> (q & 63)) & 1ull) << (t & 63);
+      r.z(t >> 6) |= ((k.z(q >> 6) >> (q & 63)) & 1ull) << (t & 63);
+    }
+  }
+  return r;
+}
+
+// D_n (rotations and reflections of a ring): the lower of the Z_n
+// representatives of the string and of its reflection, since every
+// reflection is a rotation of the one reflection above.
+template <int W>
+__device__ __forceinline__ void canon_dn(Key<W>& k, int n) {
+  Key<W> r = reflect_key<W>(k, n);
+  canon_zn<W>(k, n);
+  canon_zn<W>(r, n);
+  if (key_less<W>(r, k)) k = r;
+}
+
+// Translations of an lx x (n / lx) torus, qubit q = x + lx y: lowest digit
+// integer over all (dx, dy).  One word: a translation is a cyclic shift of
+// every row by dx (masks) and of the whole string by lx * dy.
+__device__ __forceinline__ uint64_t rot_bits(uint64_t m, int s, int n, uint64_t nmask) {
+  return s == 0 ? m : (((m << s) | (m >> (n - s))) & nmask);
+}
+
+__device__ __forceinline__ void canon_torus_w1(Key<1>& k, int n, int lx) {
+  typedef unsigned __int128 u128;
+  const int ly = n / lx;
+  const uint64_t nmask = (n == 64) ? ~0ull : ((1ull << n) - 1ull);
+  const uint64_t x = k.x(0), z = k.z(0);
+  auto dig = [](uint64_t xx, uint64_t zz) {
+    return (u128)digits32((uint32_t)xx, (uint32_t)zz) |
+           ((u128)digits32((uint32_t)(xx >> 32), (uint32_t)(zz >> 32)) << 64);
+  };
+  u128 best = dig(x, z);
+  uint64_t bx = x, bz = z;
+  for (int dx = 0; dx < lx; ++dx) {
+    // columns [0, lx - dx) move up by dx, the rest wrap down by lx - dx
+    uint64_t low = 0;
+    const uint64_t row = (lx - dx >= 64) ? ~0ull : ((1ull << (lx - dx)) - 1ull);
+    for (int y = 0; y < ly; ++y) low |= row << (lx * y);  // lx * y < n <= 64
+    const uint64_t high = nmask & ~low;
+    const uint64_t sx = dx == 0 ? x : (((x & low) << dx) | ((x & high) >> (lx - dx)));
+    const uint64_t sz = dx == 0 ? z : (((z & low) << dx) | ((z & high) >> (lx - dx)));
+    for (int dy = 0; dy < ly; ++dy) {
+      const uint64_t tx = rot_bits(sx, lx * dy, n, nmask), tz = rot_bits(sz, lx * dy, n, nmask);
+      const u128 v = dig(tx, tz);
+      if (v < best) {
+        best = v;
+        bx = tx;
+        bz = tz;
+      }
+    }
+  }
+  k.x(0) = bx;
+  k.z(0) = bz;
+}
+
+template <int W>
+__device__ __forceinline__ int torus_src(int q, int dx, int dy, int lx, int ly) {
+  int x = q % lx - dx, y = q / lx - dy;
+  x += (x < 0) ? lx : 0;
+  y += (y < 0) ? ly : 0;
+  return x + lx * y;
+}
+
+// Several words: compare translations digit by digit from the most
+// significant qubit (the letter at q comes from torus_src(q)).
+template <int W>
+__device__ __forceinline__ void canon_torus_generic(Key<W>& k, int n, int lx) {
+  const int ly = n / lx;
+  int bdx = 0, bdy = 0;
+  for (int dy = 0; dy < ly; ++dy)
+    for (int dx = 0; dx < lx; ++dx) {
+      if (dx == 0 && dy == 0) continue;
+      int cmp = 0;
+      for (int q = n - 1; q >= 0 && cmp == 0; --q) {
+        const int a = digit_at<W>(k, torus_src<W>(q, dx, dy, lx, ly));
+        const int b = digit_at<W>(k, torus_src<W>(q, bdx, bdy, lx, ly));
+        cmp = (a < b) ? -1 : ((a > b) ? 1 : 0);
+      }
+      if (cmp < 0) {
+        bdx = dx;
+        bdy = dy;
+      }
+    }
+  if (bdx == 0 && bdy == 0) return;
+  Key<W> r;
+#pragma unroll
+  for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
+  for (int q = 0; q < n; ++q) {
+    const int src = torus_src<W>(q, bdx, bdy, lx, ly);
+    r.x(q >> 6) |= ((k.x(src >> 6) >> (src & 63)) & 1ull) << (q & 63);
+    r.z(q >> 6) |= ((k.z(src >> 6) >> (src & 63)) & 1ull) << (q & 63);
+  }
+  k = r;
+}
+
+// Group codes: 0 none, 1 Z_n, 2 S_n, 3 D_n, 4 torus translations (lattice
+// width lx passed separately).
+template <int W, int G>
+__device__ __forceinline__ void canon(Key<W>& k, int n, int lx) {
+  if constexpr (G == 1) {
+    canon_zn<W>(k, n);
   } else if constexpr (G == 2) {
     canon_sn<W>(k);
+  } else if constexpr (G == 3) {
+    canon_dn<W>(k, n);
+  } else if constexpr (G == 4) {
+    if constexpr (W == 1) {
+      canon_torus_w1(k, n, lx);
+    } else {
+      canon_torus_generic<W>(k, n, lx);
+    }
   }
 }
 
@@ -390,6 +533,45 @@ __device__ __forceinline__ double overlap_zn(const Key<W>& k, const OverlapArgs&
     acc += v;
   }
   return acc / (double)n;
+}
+
+// Average of Tr[rho g r] over the elements g of D_n (2n: q -> j +- q) or of
+// the torus translations (lx * ly: (x, y) -> (x + dx, y + dy)).
+template <int W>
+__device__ __forceinline__ double overlap_group(const Key<W>& k, const OverlapArgs& a) {
+  const int n = a.n;
+  const bool dn = a.group == 3;
+  const int lx = dn ? 1 : a.lx, ly = dn ? 1 : n / a.lx;
+  const int n_el = dn ? 2 * n : n;
+  double acc = 0.0;
+  for (int e = 0; e < n_el; ++e) {
+    const int j = dn ? (e >> 1) : 0, refl = dn ? (e & 1) : 0;
+    const int dx = dn ? 0 : e % lx, dy = dn ? 0 : e / lx;
+    double v = 1.0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint64_t m = k.x(w) | k.z(w);
+      while (m) {
+        const int b = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const int q = 64 * w + b;
+        int t;
+        if (dn) {
+          t = refl ? (j - q) : (j + q);
+          t %= n;
+          t += (t < 0) ? n : 0;
+        } else {
+          const int x = (q % lx + dx) % lx, y = (q / lx + dy) % ly;
+          t = x + lx * y;
+        }
+        const int xb = (int)((k.x(w) >> b) & 1ull), zb = (int)((k.z(w) >> b) & 1ull);
+        const int l = xb ? (zb ? 1 : 0) : 2;  // X -> 0, Y -> 1, Z -> 2
+        v *= a.bloch[3 * t + l];
+      }
+    }
+    acc += v;
+  }
+  return acc / (double)n_el;
 }
 
 template <int W>

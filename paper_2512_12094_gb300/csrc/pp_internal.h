@@ -87,7 +87,9 @@ struct GateArgs {
 
 struct OverlapArgs {
   int n;
-  int group;        // 0 plain, 1 Z_n orbit average, 2 S_n table lookup
+  int group;        // 0 plain, 1 Z_n orbit average, 2 S_n table lookup,
+                    // 3 D_n / 4 torus average over the group elements
+  int lx;           // torus lattice width (group 4)
   int basis;        // 1: rho is a computational basis state given by bits
   uint64_t bits[kMaxW];
   const double* bloch;     // [n][3] device array (product mode)
@@ -164,6 +166,10 @@ cudaError_t launch_pack_keys(int W, int n, int grid, cudaStream_t s, const uint6
 
 // Message returned by pp_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
+
+// Is code a known group (pp_symmetry, with the torus width above the low
+// byte for PP_SYM_TORUS) for n qubits?
+bool valid_group_code(int code, int n);
 
 // ------------------------------------------------------- batched launchers
 // Same contracts as the single-column kernels above, on B-column rows.

@@ -468,7 +468,7 @@ template <int W, int G>
 __global__ void __launch_bounds__(kBlock)
     merge_insert_kernel(const uint64_t* __restrict__ src_keys, const double* __restrict__ src_coef,
                         uint64_t count, const unsigned long long* count_dev, int skip_zero,
-                        int wmax, int n, DevTable dst, DevCtl* ctl) {
+                        int wmax, int n, int lx, DevTable dst, DevCtl* ctl) {
   const uint64_t T = count_dev ? *count_dev : count;
   unsigned err = 0;
   unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kBlock)
     if (skip_zero && c == 0.0) continue;
     Key<W> K = ld_key<W>(src_keys, i);
     if (wmax >= 0 && weight(K) > wmax) continue;
-    canon<W, G>(K, n);
+    canon<W, G>(K, n, lx);
     const uint64_t h = key_hash(K);
     const uint32_t tag = tag_of(h);
     uint64_t pos = h & dst.imask;
@@ -615,11 +615,11 @@ __global__ void __launch_bounds__(kBlock)
 
 template <int W, int G>
 __global__ void __launch_bounds__(kBlock)
-    canon_inplace_kernel(uint64_t* keys, const uint64_t* keys_in, uint64_t count, int n) {
+    canon_inplace_kernel(uint64_t* keys, const uint64_t* keys_in, uint64_t count, int n, int lx) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     Key<W> k = ld_key_cg<W>(keys_in, i);
-    canon<W, G>(k, n);
+    canon<W, G>(k, n, lx);
     st_key<W>(keys, i, k);
   }
 }
@@ -666,6 +666,8 @@ __global__ void __launch_bounds__(kBlock)
     double ov;
     if (a.group == 1)
       ov = overlap_zn<W>(k, a);
+    else if (a.group == 3 || a.group == 4)
+      ov = overlap_group<W>(k, a);
     else if (a.group == 2)
       ov = overlap_sn<W>(k, a);
     else
@@ -849,22 +851,20 @@ cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cud
                                   const uint64_t* src_keys, const double* src_coef,
                                   uint64_t count, const unsigned long long* count_dev,
                                   int skip_zero, DevTable dst, DevCtl* ctl) {
-  switch (group) {
-    case 0:
-      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 0><<<grid, kBlock, 0, s>>>(
-                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
-      break;
-    case 1:
-      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 1><<<grid, kBlock, 0, s>>>(
-                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
-      break;
-    case 2:
-      PP_DISPATCH_W(W, (merge_insert_kernel<WW, 2><<<grid, kBlock, 0, s>>>(
-                           src_keys, src_coef, count, count_dev, skip_zero, wmax, n, dst, ctl)));
-      break;
+  const int lx = group >> 8;  // group code: kind | (torus width << 8)
+#define PP_MERGE_G(GG)                                                                     \
+  PP_DISPATCH_W(W, (merge_insert_kernel<WW, GG><<<grid, kBlock, 0, s>>>(                   \
+                       src_keys, src_coef, count, count_dev, skip_zero, wmax, n, lx, dst, ctl)))
+  switch (group & 0xFF) {
+    case 0: PP_MERGE_G(0); break;
+    case 1: PP_MERGE_G(1); break;
+    case 2: PP_MERGE_G(2); break;
+    case 3: PP_MERGE_G(3); break;
+    case 4: PP_MERGE_G(4); break;
     default:
       return cudaErrorInvalidValue;
   }
+#undef PP_MERGE_G
   return cudaGetLastError();
 }
 
@@ -883,13 +883,17 @@ cudaError_t launch_compact(int W, int grid, cudaStream_t s, DevTable src, uint64
 
 cudaError_t launch_canon_inplace(int W, int group, int n, int grid, cudaStream_t s,
                                  uint64_t* keys, const uint64_t* keys_in, uint64_t count) {
-  if (group == 1) {
-    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 1><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
-  } else if (group == 2) {
-    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 2><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
-  } else {
-    PP_DISPATCH_W(W, (canon_inplace_kernel<WW, 0><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n)));
+  const int lx = group >> 8;
+#define PP_CANON_G(GG) \
+  PP_DISPATCH_W(W, (canon_inplace_kernel<WW, GG><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n, lx)))
+  switch (group & 0xFF) {
+    case 1: PP_CANON_G(1); break;
+    case 2: PP_CANON_G(2); break;
+    case 3: PP_CANON_G(3); break;
+    case 4: PP_CANON_G(4); break;
+    default: PP_CANON_G(0); break;
   }
+#undef PP_CANON_G
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ extern "C" pp_status pp_merge_terms_noalloc(int n_qubits, int symmetry, int64_t 
     set_last_error("pp_merge_terms_noalloc: n_qubits must be in 1..256");
     return PP_ERR_ARG;
   }
-  if (symmetry < PP_SYM_NONE || symmetry > PP_SYM_SN) {
+  if (!valid_group_code(symmetry, n_qubits)) {
     set_last_error("pp_merge_terms_noalloc: unknown symmetry");
     return PP_ERR_ARG;
   }

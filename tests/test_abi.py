@@ -48,7 +48,8 @@ def test_config_default(lib):
 
 
 @pytest.mark.parametrize("fields", [dict(n_qubits=0), dict(n_qubits=257), dict(batch=0),
-                                    dict(batch=513), dict(symmetry=3), dict(coef_type=2),
+                                    dict(batch=513), dict(symmetry=5), dict(symmetry=4 | (3 << 8)),
+                                    dict(symmetry=4), dict(symmetry=1 | (2 << 8)), dict(coef_type=2),
                                     dict(coeff_eps=-1.0), dict(noise_mode=7),
                                     dict(batch=4, noise_mode=2, noise_p=0.1),
                                     dict(coef_type=1, noise_mode=2, noise_p=0.1)])
@@ -61,6 +62,16 @@ def test_create_rejects_bad_config_without_gpu(lib, fields):
     assert st == 1  # PP_ERR_ARG
     assert h.value is None
     assert lib.pp_last_error().decode() != ""
+
+
+def test_group_codes_in_the_header_match_the_binding(lib):
+    txt = open(os.path.join(ROOT, "include", "pp.h")).read()
+    for name, value in (("PP_SYM_ZN", pp.SYM_ZN), ("PP_SYM_SN", pp.SYM_SN),
+                        ("PP_SYM_DN", pp.SYM_DN), ("PP_SYM_TORUS", pp.SYM_TORUS)):
+        assert re.search(r"\b%s = %d\b" % (name, value), txt), name
+    assert pp.sym_torus(4) == 4 + 4 * 256
+    # a torus width that does not divide n is rejected before any CUDA call
+    assert lib.pp_canonical_keys(8, pp.sym_torus(3), 1, None, None, None) == 1
 
 
 def test_stateless_calls_validate_arguments(lib):
