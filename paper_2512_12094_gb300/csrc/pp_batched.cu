@@ -126,11 +126,14 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
           const uint64_t h = key_hash(R);
           jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
         }
-        n_ac += aliveQ;
         neg = sigma_of<W>(g, Q) < 0;
+        // live anticommuting rows from values before the gate: the owner
+        // counts a stored pair, anyone else only itself (as in the FP64 kernel)
+        if (jr < 0) n_ac += aliveQ;
         if (jr >= 0) {
           if (pw == 0) {
             aliveR = __ldcg(t.alive + jr) != 0;
+            n_ac += (unsigned long long)aliveQ + (unsigned long long)aliveR;
             if (aliveQ || aliveR) {
               act = 2;
               if (noise) {

@@ -181,9 +181,15 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
           const uint64_t h = key_hash(R);
           jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
         }
-        n_ac += liveQ;
         const bool neg = sigma_of<W>(g, Qk) < 0;  // i P Q = -R
         const double cR = (jr >= 0 && pw == 0) ? ld_coef(t.coef, jr) : 0.0;
+        // live anticommuting strings, counted from values before the gate: the
+        // owner counts a stored pair (its partner may be rewriting the other
+        // member meanwhile), anyone else counts only itself
+        if (jr >= 0)
+          n_ac += pw == 0 ? (unsigned long long)liveQ + (unsigned long long)!is_dead(cR) : 0ull;
+        else
+          n_ac += liveQ;
         // owner with its partner stored, or a live string whose partner is new
         const bool own = jr >= 0 && pw == 0 && (liveQ || !is_dead(cR));
         const bool birth = jr == -1 && liveQ;

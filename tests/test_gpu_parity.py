@@ -117,17 +117,23 @@ def test_truncation_bitexact(eps, wmax):
 @pytest.mark.parametrize("symmetry", [0, 1])
 def test_launch_paths_agree(symmetry):
     """Cooperative layer kernel, per-gate kernels from CUDA graphs (PDL) and
-    per-gate direct launches give bit-identical tables."""
-    wl = pi.config1_ring(n=16, steps=5, eps=1e-5, max_weight=8)
-    runs = []
+    per-gate direct launches give bit-identical tables and the same update
+    statistics (live terms and live anticommuting terms entering each gate,
+    counted from values before the gate, so no path depends on timing)."""
+    wl = pi.config1_ring(n=32 if symmetry == 0 else 16, steps=5, eps=1e-4 if symmetry == 0 else 1e-5,
+                         max_weight=10 if symmetry == 0 else 8)
+    runs, stats = [], []
     for kw in (dict(layer_kernel=True), dict(layer_kernel=False, use_graphs=True),
-               dict(layer_kernel=False, use_graphs=False)):
+               dict(layer_kernel=False, use_graphs=False), dict(layer_kernel=True)):
         p = pp.Propagator.from_workload(wl, symmetry=symmetry, **kw)
         p.run(wl)
         runs.append(as_dict(*p.export()))
+        st = p.stats()
+        stats.append((st["gate_updates"], st["anticommuting_terms"]))
         p.close()
+    assert len(set(stats)) == 1, stats
     if symmetry == 0:
-        assert runs[0] == runs[1] == runs[2]
+        assert runs[0] == runs[1] == runs[2] == runs[3]
     else:  # merges sum with atomics: same keys, coefficients to rounding
         for r in runs[1:]:
             assert set(r) == set(runs[0])
