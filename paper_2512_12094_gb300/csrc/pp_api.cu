@@ -104,6 +104,7 @@ struct pp_ctx {
   size_t esize = 8;      // bytes per row element
   size_t row_bytes() const { return batched ? (size_t)B * esize + 1 : 8; }
   std::vector<ArgsEntry> cs_cache;  // per-gate cos/sin columns (batched)
+  std::vector<std::vector<unsigned char>> sym_ok;  // layers (gates + angles) already validated
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int sms = 1;
@@ -249,13 +250,10 @@ int grid_for(pp_ctx* c, uint64_t items, int per_thread) {
 }
 
 // Set n_next (append cursor) and n_live before a merge or compaction into
-// the spare table.
+// the spare table (a one-thread kernel on the stream: no host round trip).
 pp_status ctl_prepare_insert(pp_ctx* c, unsigned long long first_free) {
-  unsigned long long nn = first_free;
-  long long live = 0;
-  PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_next, &nn, 8, cudaMemcpyHostToDevice, c->stream));
-  PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_live, &live, 8, cudaMemcpyHostToDevice, c->stream));
-  PP_CUDA(cudaStreamSynchronize(c->stream));  // the sources live on the host stack
+  PP_CUDA(launch_ctl_insert(c->stream, c->d_ctl, first_free));
+  c->launches += 1;
   return PP_OK;
 }
 
@@ -1103,7 +1101,18 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
   std::vector<GateArgs> args;
   std::vector<int> src_t;
   PP_TRY(build_gates(c, n_gates, gates, theta, args, src_t));
+  // a layer already validated for this context (same gates and angles: a
+  // Trotter step repeated) is not checked again
+  std::vector<unsigned char> sig;
+  bool validated = false;
   if (c->cfg.symmetry != PP_SYM_NONE && c->cfg.check_symmetry && n_gates > 0) {
+    sig.resize((size_t)n_gates * (sizeof(pp_pauli) + sizeof(double) * c->B));
+    memcpy(sig.data(), gates, (size_t)n_gates * sizeof(pp_pauli));
+    memcpy(sig.data() + (size_t)n_gates * sizeof(pp_pauli), theta,
+           (size_t)n_gates * sizeof(double) * c->B);
+    for (const auto& v : c->sym_ok) validated |= (v == sig);
+  }
+  if (c->cfg.symmetry != PP_SYM_NONE && c->cfg.check_symmetry && n_gates > 0 && !validated) {
     std::vector<HKey> ks;
     for (int t = 0; t < n_gates; ++t) {
       HKey k(2 * c->W);
@@ -1119,6 +1128,8 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
       if (!multiset_invariant(c->cfg.symmetry, c->n, c->W, ks, vs, 0.0))
         return fail(PP_ERR_SYMMETRY, "layer gate multiset is not invariant under the group");
     }
+    if (c->sym_ok.size() >= 8) c->sym_ok.erase(c->sym_ok.begin());
+    c->sym_ok.push_back(std::move(sig));
   }
   PP_TRY(ensure_merged(c));
   // With a memory budget a layer may stop with PP_ERR_CAPACITY part way

@@ -102,6 +102,9 @@ struct OverlapArgs {
 // Before the first gate of a (resumed) layer: slot (first+2)%3 <- (n_terms,
 // n_live), counters of slot first%3 cleared, stall cleared.
 cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate);
+// Before a merge or compaction into a fresh table: append cursor n_next <-
+// first_free, live count <- 0 (stream ordered, no host round trip).
+cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free);
 // After the gates of a layer (n_gates of them): (n_terms, n_live) <- the state
 // after the last gate that ran.
 cudaError_t launch_chain_finish(cudaStream_t s, DevCtl* ctl, unsigned n_gates);

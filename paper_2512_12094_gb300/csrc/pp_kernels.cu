@@ -448,6 +448,11 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
   }
 }
 
+__global__ void ctl_insert_kernel(DevCtl* ctl, unsigned long long first_free) {
+  ctl->n_next = first_free;
+  ctl->n_live = 0;
+}
+
 __global__ void chain_init_kernel(DevCtl* ctl, unsigned first_gate) {
   const int q = (int)((first_gate + 2u) % 3u), p = (int)(first_gate % 3u);
   ctl->bar_root = 0;
@@ -776,6 +781,11 @@ __global__ void __launch_bounds__(kBlock)
     case 4: { constexpr int WW = 4; __VA_ARGS__; break; } \
     default: return cudaErrorInvalidValue;        \
   }
+
+cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free) {
+  ctl_insert_kernel<<<1, 1, 0, s>>>(ctl, first_free);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate) {
   chain_init_kernel<<<1, 1, 0, s>>>(ctl, first_gate);
