@@ -137,6 +137,7 @@ struct pp_ctx {
   int overlap_grid = 0;
   int64_t launches = 0;
   std::vector<cudaEvent_t> ev_start, ev_end;  // per gate position (profile_kernels)
+  double last_growth = 2.0;  // stored entries after / before the gates of the last layer
   double gate_ms = 0.0;
   int64_t gates_timed = 0;
 };
@@ -313,16 +314,23 @@ pp_status ensure_capacity(pp_ctx* c, uint64_t need) {
 }
 
 // Make room before (or in the middle of) a layer: drop truncated entries when
-// they are a quarter of the table or more, then make the capacity at least 4x
-// the entries, so that a stall (a gate needs room for twice its input) only
-// happens once a layer has doubled the table.  Every stall costs a host round
-// trip, a compaction and a relaunch, so growth is generous; untouched
-// capacity costs memory, not bandwidth.
-pp_status make_room(pp_ctx* c) {
+// they are a quarter of the table or more, then make sure the capacity holds
+// factor x the entries.  The caller derives factor from how much the previous
+// layer grew the table, so that a layer rarely stalls (every stall costs a
+// host round trip, a compaction and a relaunch); untouched capacity costs
+// memory, not bandwidth.  Under a memory budget the growth falls back to the
+// least that lets the next gate run.
+pp_status make_room(pp_ctx* c, uint64_t factor = 2) {
   if (c->cfg.coeff_eps > 0.0 && c->n_terms > 0 && 4 * (c->n_terms - c->n_live) >= c->n_terms)
     PP_TRY(compact_into(c, 1 - c->active, 0.0, -1));
-  if (2 * c->n_terms <= c->buf[c->active].cap) return PP_OK;
-  return ensure_capacity(c, c->n_terms * 4);
+  const uint64_t cap = c->buf[c->active].cap;
+  if (factor * c->n_terms <= cap) return PP_OK;
+  const uint64_t least = c->n_terms * 4;
+  const uint64_t generous = std::max<uint64_t>(least, factor * c->n_terms * 3 / 2);
+  const pp_status st = ensure_capacity(c, generous);
+  if (st != PP_ERR_CAPACITY || generous == least) return st;
+  if (2 * c->n_terms <= cap) return PP_OK;  // the next gate fits; grow at a stall
+  return ensure_capacity(c, least);
 }
 
 // Accumulate the active table (after optional canonicalisation) into the
@@ -968,7 +976,11 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
                               desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
     c->launches += 1;
   }
-  PP_TRY(make_room(c));
+  // room for twice the growth the previous layer showed (at least doubling)
+  const uint64_t factor =
+      std::max<uint64_t>(2, (uint64_t)std::ceil(2.0 * 1.25 * std::max(1.0, c->last_growth)));
+  PP_TRY(make_room(c, factor));
+  const uint64_t n_start = std::max<uint64_t>(c->n_terms, 1);
   const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
   const bool layered = c->cfg.layer_kernel && c->layer_bps > 0 && !c->batched;
   if (c->batched && !args.empty()) PP_TRY(batched_columns(c, args, src_t, theta));
@@ -1017,9 +1029,10 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       c->n_live = c->h_ctl->n_live;
       if (!c->h_ctl->stall) break;
       // gate `end` found too little room: compact and grow, then resume there
-      PP_TRY(make_room(c));
+      PP_TRY(make_room(c, std::max<uint64_t>(factor, 4)));
       first = end;
     }
+    c->last_growth = (double)c->n_terms / (double)n_start;
   }
   if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE) {
     PP_TRY(merge_active(c, c->cfg.symmetry));

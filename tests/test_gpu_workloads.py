@@ -204,7 +204,7 @@ def test_capacity_error_restores_the_context(batch):
     for layer in reversed(range(8)):
         gx, gz, th = wl.circuit.gate_arrays(layer)
         ref.apply_layer(gx, gz, cols(th), True)
-    budget = ref.stats()["device_bytes"] // 2  # the run outgrows this part way
+    budget = ref.stats()["device_bytes"] // 4  # the run outgrows this part way
     ref.close()
     ref, p = make(0), make(budget)
     bloch = wl.state.bloch
