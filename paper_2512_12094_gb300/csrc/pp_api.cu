@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -144,9 +145,67 @@ struct pp_ctx {
 
 namespace {
 
+// The library's stream-ordered memory pool on the current device, created
+// once.  It keeps freed memory mapped (no release threshold), so tables
+// that are freed and allocated again -- a table moved when it grows, the
+// next context of a server -- reuse memory instead of mapping it anew at
+// every synchronise, as the default pool would.  The memory stays with the
+// process until it exits.
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
+// Pinned host blocks of the per-context mirrors, kept for reuse: freeing
+// pinned memory waits for the whole device.
+std::mutex g_pinned_mu;
+std::vector<std::pair<size_t, void*>> g_pinned_free;
+
+cudaError_t pinned_get(void** p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    for (size_t k = 0; k < g_pinned_free.size(); ++k) {
+      if (g_pinned_free[k].first == bytes) {
+        *p = g_pinned_free[k].second;
+        g_pinned_free.erase(g_pinned_free.begin() + (long)k);
+        return cudaSuccess;
+      }
+    }
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  if (g_pinned_free.size() < 256) {
+    g_pinned_free.emplace_back(bytes, p);
+    return;
+  }
+  cudaFreeHost(p);
+}
+
 pp_status dmalloc(pp_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+  cudaMemPool_t pool = lib_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, c->stream)
+                       : cudaMallocAsync(p, bytes, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
   c->bytes += bytes;
   return PP_OK;
@@ -539,8 +598,8 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   pp_status st;
   if ((st = dmalloc(c, (void**)&c->d_desc, 3 * sizeof(DevTable))) != PP_OK) return cleanup(st);
   if ((st = dmalloc(c, (void**)&c->d_ctl, sizeof(DevCtl))) != PP_OK) return cleanup(st);
-  if (cudaMallocHost((void**)&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->h_out, sizeof(double) * cfg->batch) != cudaSuccess)
+  if (pinned_get((void**)&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
+      pinned_get((void**)&c->h_out, sizeof(double) * cfg->batch) != cudaSuccess)
     return cleanup(fail(PP_ERR_OOM, "pinned host allocation failed"));
   memset(c->h_ctl, 0, sizeof(DevCtl));
   c->overlap_grid = c->sms * 4;
@@ -1099,8 +1158,8 @@ pp_status pp_destroy(pp_ctx* c) {
   dfree(c, c->d_sn, sn);
   dfree(c, c->d_sn_work, sn);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->h_ctl) cudaFreeHost(c->h_ctl);
-  if (c->h_out) cudaFreeHost(c->h_out);
+  pinned_put(c->h_ctl, sizeof(DevCtl));
+  pinned_put(c->h_out, sizeof(double) * c->B);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return PP_OK;
