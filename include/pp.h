@@ -143,6 +143,18 @@ pp_status pp_create(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
 pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
                            const uint64_t* z, const double* coef, pp_ctx** out);
 
+/* Replace the operator held by ctx with sum_i coef[i] s_i, for example a
+ * table saved with pp_export, to resume a propagation (checkpoint and
+ * restart).  Host arrays in pp_create's layout: x, z [n_terms][W],
+ * coef [n_terms][batch], only read during the call.  Identical strings
+ * accumulate and the truncation rules apply, as at creation.  With a group,
+ * strings are folded into their representatives and the operator is taken
+ * to be invariant -- the form pp_export returns for such a context.
+ * Errors: PP_ERR_ARG (null arrays, n_terms < 0, bits at or above n_qubits),
+ * PP_ERR_CAPACITY, PP_ERR_OOM, PP_ERR_CUDA. */
+pp_status pp_import(pp_ctx* ctx, int64_t n_terms, const uint64_t* x, const uint64_t* z,
+                    const double* coef);
+
 /* Release every device and host resource of ctx.  NULL is accepted. */
 pp_status pp_destroy(pp_ctx* ctx);
 
@@ -191,6 +203,12 @@ pp_status pp_truncate(pp_ctx* ctx, double eps, int max_weight);
  * in a fixed order.  out receives `batch` doubles (one per angle set).
  * Errors: PP_ERR_SYMMETRY when neither rho nor the ingested O is invariant. */
 pp_status pp_expect(pp_ctx* ctx, const double* bloch, double* out);
+
+/* pp_expect for the computational basis state |b_0 ... b_{n-1}> (Alg. 1 step
+ * 3 with rho a basis state): bits[q] in {0, 1}; the same as pp_expect with
+ * Bloch vectors (0, 0, 1 - 2 b_q).  out: batch doubles.  Same errors as
+ * pp_expect. */
+pp_status pp_expect_basis(pp_ctx* ctx, const uint8_t* bits, double* out);
 
 /* Number of live terms and of stored table entries. */
 pp_status pp_num_terms(pp_ctx* ctx, int64_t* live, int64_t* stored);

@@ -141,6 +141,8 @@ _SIGS = {
     "pp_merge": [_vp],
     "pp_truncate": [_vp, ctypes.c_double, ctypes.c_int],
     "pp_expect": [_vp, _vp, _f64p],
+    "pp_expect_basis": [_vp, _vp, _f64p],
+    "pp_import": [_vp, ctypes.c_int64, _vp, _vp, _vp],
     "pp_num_terms": [_vp, _i64p, _i64p],
     "pp_export": [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64p],
     "pp_stats": [_vp, ctypes.POINTER(pp_stats_t)],
@@ -272,6 +274,23 @@ def pp_expect(ctx, bloch, batch: int = 1):
     out = np.zeros(batch, dtype=np.float64)
     _check(load().pp_expect(ctx, _ptr(b), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return float(out[0]) if batch == 1 else out
+
+
+def pp_expect_basis(ctx, bits, batch: int = 1):
+    """Tr[rho O] for the computational basis state with bits[q] in {0, 1}."""
+    b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1))
+    out = np.zeros(batch, dtype=np.float64)
+    _check(load().pp_expect_basis(ctx, _ptr(b), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return float(out[0]) if batch == 1 else out
+
+
+def pp_import(ctx, n_qubits: int, x, z, coef, batch: int = 1):
+    """Replace the context's operator by the given terms (pp_create's layout)."""
+    W = (n_qubits + 63) // 64
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64).reshape(-1, W))
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.uint64).reshape(-1, W))
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, batch))
+    _check(load().pp_import(ctx, c.shape[0], _ptr(x), _ptr(z), _ptr(c)))
 
 
 def pp_num_terms(ctx):

@@ -555,6 +555,122 @@ pp_status validate_config(const pp_config* cfg) {
   return PP_OK;
 }
 
+// Replace the operator held by the active table with sum_i coef[i] s_i
+// (arrays on the host or, with on_device, on the device): check the strings,
+// record whether the observable is invariant under the group, and accumulate
+// the strings (as representatives when a group is set) with truncation.
+pp_status ingest_terms(pp_ctx* c, int64_t n_terms, const uint64_t* x, const uint64_t* z,
+                       const double* coef, bool on_device, bool assume_invariant = false) {
+  const int W = c->W;
+  pp_status st;
+  // Observable invariance (host copy needed for the check).
+  std::vector<uint64_t> hx, hz;
+  std::vector<double> hc;
+  if (n_terms > 0) {
+    hx.resize((size_t)n_terms * W);
+    hz.resize((size_t)n_terms * W);
+    hc.resize((size_t)n_terms * c->B);
+    if (on_device) {
+      if (cudaMemcpyAsync(hx.data(), x, hx.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaMemcpyAsync(hz.data(), z, hz.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaMemcpyAsync(hc.data(), coef, hc.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(PP_ERR_CUDA, "reading device term arrays failed");
+    } else {
+      memcpy(hx.data(), x, hx.size() * 8);
+      memcpy(hz.data(), z, hz.size() * 8);
+      memcpy(hc.data(), coef, hc.size() * 8);
+    }
+    for (int64_t i = 0; i < n_terms; ++i)
+      if (key_has_bits_beyond(&hx[i * W], &hz[i * W], c->n, W))
+        return fail(PP_ERR_ARG, "a string has bits at or above n_qubits");
+  }
+  if (c->cfg.symmetry != PP_SYM_NONE && assume_invariant) {
+    c->obs_invariant = true;  // terms in representative form stand for an invariant operator
+  } else if (c->cfg.symmetry != PP_SYM_NONE) {
+    // the observable is invariant when every column is
+    c->obs_invariant = true;
+    for (int b = 0; b < c->B && c->obs_invariant; ++b) {
+      std::map<HKey, double> acc;
+      for (int64_t i = 0; i < n_terms; ++i) {
+        HKey k(2 * W);
+        for (int j = 0; j < W; ++j) {
+          k[j] = hx[i * W + j];
+          k[W + j] = hz[i * W + j];
+        }
+        acc[k] += hc[(size_t)i * c->B + b];
+      }
+      std::vector<HKey> ks;
+      std::vector<double> vs;
+      for (auto& kv : acc) {
+        ks.push_back(kv.first);
+        vs.push_back(kv.second);
+      }
+      c->obs_invariant = multiset_invariant(c->cfg.symmetry, c->n, W, ks, vs, 1e-12);
+    }
+  }
+
+  // Ingest: pack, then accumulate (with representatives when a group is set)
+  // into the active table, which starts empty.
+  PP_CUDA(cudaMemsetAsync(c->buf[c->active].index, 0, (size_t)c->buf[c->active].icap * 8,
+                          c->stream));
+  if (n_terms == 0) {
+    PP_TRY(ctl_prepare_insert(c, 0));
+    PP_TRY(ctl_commit(c));
+  }
+  if (n_terms > 0) {
+    uint64_t* d_keys = nullptr;
+    double* d_coef = nullptr;
+    unsigned* d_bad = nullptr;
+    if ((st = dmalloc(c, (void**)&d_keys, (size_t)n_terms * 16 * W)) != PP_OK ||
+        (st = dmalloc(c, (void**)&d_coef, hc.size() * 8)) != PP_OK)
+      return st;
+    std::vector<uint64_t> packed((size_t)n_terms * 2 * W);
+    for (int64_t i = 0; i < n_terms; ++i)
+      for (int j = 0; j < W; ++j) {
+        packed[i * 2 * W + j] = hx[i * W + j];
+        packed[i * 2 * W + W + j] = hz[i * W + j];
+      }
+    (void)d_bad;
+    if (cudaMemcpyAsync(d_keys, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_coef, hc.data(), hc.size() * 8, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+      return fail(PP_ERR_CUDA, "term upload failed");
+    if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return st;
+    cudaError_t e;
+    if (c->batched) {
+      double* acc = nullptr;
+      const size_t acc_bytes = (size_t)n_terms * c->B * sizeof(double);
+      if ((st = dmalloc(c, (void**)&acc, acc_bytes)) != PP_OK) return st;
+      e = cudaMemsetAsync(acc, 0, acc_bytes, c->stream);
+      if (e == cudaSuccess)
+        e = launch_merge_batched(W, c->cfg.symmetry, c->n, c->cfg.max_weight, 0,
+                                 grid_for(c, n_terms, 32), c->stream, d_keys, d_coef, nullptr,
+                                 (uint64_t)n_terms, desc_of(c, c->buf[c->active]), acc, c->d_ctl);
+      if (e == cudaSuccess)
+        e = launch_finalize_batched(grid_for(c, n_terms, 32), c->stream, desc_of(c, c->buf[c->active]),
+                                    acc, c->d_ctl, c->cfg.coeff_eps);
+      if (e != cudaSuccess) return cuda_fail(e, "batched ingest");
+      if ((st = ctl_commit(c)) != PP_OK) return st;
+      dfree(c, acc, acc_bytes);
+    } else {
+      e = launch_merge_insert(W, c->cfg.symmetry, c->n, c->cfg.max_weight, grid_for(c, n_terms, 4),
+                              c->stream, d_keys, d_coef, (uint64_t)n_terms, nullptr, 0,
+                              desc_of(c, c->buf[c->active]), c->d_ctl);
+      if (e != cudaSuccess) return cuda_fail(e, "merge_insert");
+      e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c, c->buf[c->active]), c->d_ctl,
+                          c->cfg.coeff_eps);
+      if (e != cudaSuccess) return cuda_fail(e, "finalize");
+      if ((st = ctl_commit(c)) != PP_OK) return st;
+    }
+    dfree(c, d_keys, (size_t)n_terms * 16 * W);
+    dfree(c, d_coef, hc.size() * 8);
+  }
+  c->merged = true;
+  return PP_OK;
+}
+
 pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
                         const uint64_t* z, const double* coef, bool on_device, pp_ctx** out) {
   if (!out) return fail(PP_ERR_ARG, "out is null");
@@ -631,101 +747,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   c->active = 0;
   if ((st = publish_desc(c)) != PP_OK) return cleanup(st);
 
-  // Observable invariance (host copy needed for the check).
-  std::vector<uint64_t> hx, hz;
-  std::vector<double> hc;
-  if (n_terms > 0) {
-    hx.resize((size_t)n_terms * W);
-    hz.resize((size_t)n_terms * W);
-    hc.resize((size_t)n_terms * c->B);
-    if (on_device) {
-      if (cudaMemcpyAsync(hx.data(), x, hx.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-          cudaMemcpyAsync(hz.data(), z, hz.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-          cudaMemcpyAsync(hc.data(), coef, hc.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-          cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return cleanup(fail(PP_ERR_CUDA, "reading device term arrays failed"));
-    } else {
-      memcpy(hx.data(), x, hx.size() * 8);
-      memcpy(hz.data(), z, hz.size() * 8);
-      memcpy(hc.data(), coef, hc.size() * 8);
-    }
-    for (int64_t i = 0; i < n_terms; ++i)
-      if (key_has_bits_beyond(&hx[i * W], &hz[i * W], c->n, W))
-        return cleanup(fail(PP_ERR_ARG, "a string has bits at or above n_qubits"));
-  }
-  if (cfg->symmetry != PP_SYM_NONE) {
-    // the observable is invariant when every column is
-    c->obs_invariant = true;
-    for (int b = 0; b < c->B && c->obs_invariant; ++b) {
-      std::map<HKey, double> acc;
-      for (int64_t i = 0; i < n_terms; ++i) {
-        HKey k(2 * W);
-        for (int j = 0; j < W; ++j) {
-          k[j] = hx[i * W + j];
-          k[W + j] = hz[i * W + j];
-        }
-        acc[k] += hc[(size_t)i * c->B + b];
-      }
-      std::vector<HKey> ks;
-      std::vector<double> vs;
-      for (auto& kv : acc) {
-        ks.push_back(kv.first);
-        vs.push_back(kv.second);
-      }
-      c->obs_invariant = multiset_invariant(cfg->symmetry, c->n, W, ks, vs, 1e-12);
-    }
-  }
-
-  // Ingest: pack, then accumulate (with representatives when a group is set).
-  if (n_terms > 0) {
-    uint64_t* d_keys = nullptr;
-    double* d_coef = nullptr;
-    unsigned* d_bad = nullptr;
-    if ((st = dmalloc(c, (void**)&d_keys, (size_t)n_terms * 16 * W)) != PP_OK ||
-        (st = dmalloc(c, (void**)&d_coef, hc.size() * 8)) != PP_OK)
-      return cleanup(st);
-    std::vector<uint64_t> packed((size_t)n_terms * 2 * W);
-    for (int64_t i = 0; i < n_terms; ++i)
-      for (int j = 0; j < W; ++j) {
-        packed[i * 2 * W + j] = hx[i * W + j];
-        packed[i * 2 * W + W + j] = hz[i * W + j];
-      }
-    (void)d_bad;
-    if (cudaMemcpyAsync(d_keys, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(d_coef, hc.data(), hc.size() * 8, cudaMemcpyHostToDevice, c->stream) !=
-            cudaSuccess)
-      return cleanup(fail(PP_ERR_CUDA, "term upload failed"));
-    if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return cleanup(st);
-    cudaError_t e;
-    if (c->batched) {
-      double* acc = nullptr;
-      const size_t acc_bytes = (size_t)n_terms * c->B * sizeof(double);
-      if ((st = dmalloc(c, (void**)&acc, acc_bytes)) != PP_OK) return cleanup(st);
-      e = cudaMemsetAsync(acc, 0, acc_bytes, c->stream);
-      if (e == cudaSuccess)
-        e = launch_merge_batched(W, cfg->symmetry, c->n, cfg->max_weight, 0,
-                                 grid_for(c, n_terms, 32), c->stream, d_keys, d_coef, nullptr,
-                                 (uint64_t)n_terms, desc_of(c, c->buf[0]), acc, c->d_ctl);
-      if (e == cudaSuccess)
-        e = launch_finalize_batched(grid_for(c, n_terms, 32), c->stream, desc_of(c, c->buf[0]),
-                                    acc, c->d_ctl, cfg->coeff_eps);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "batched ingest"));
-      if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
-      dfree(c, acc, acc_bytes);
-    } else {
-      e = launch_merge_insert(W, cfg->symmetry, c->n, cfg->max_weight, grid_for(c, n_terms, 4),
-                              c->stream, d_keys, d_coef, (uint64_t)n_terms, nullptr, 0,
-                              desc_of(c, c->buf[0]), c->d_ctl);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "merge_insert"));
-      e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c, c->buf[0]), c->d_ctl,
-                          cfg->coeff_eps);
-      if (e != cudaSuccess) return cleanup(cuda_fail(e, "finalize"));
-      if ((st = ctl_commit(c)) != PP_OK) return cleanup(st);
-    }
-    dfree(c, d_keys, (size_t)n_terms * 16 * W);
-    dfree(c, d_coef, hc.size() * 8);
-  }
+  if ((st = ingest_terms(c, n_terms, x, z, coef, on_device)) != PP_OK) return cleanup(st);
   *out = c;
   return PP_OK;
 }
@@ -1132,6 +1154,16 @@ pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t
   return create_common(cfg, n_terms, x, z, coef, true, out);
 }
 
+pp_status pp_import(pp_ctx* c, int64_t n_terms, const uint64_t* x, const uint64_t* z,
+                    const double* coef) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (n_terms < 0) return fail(PP_ERR_ARG, "n_terms < 0");
+  if (n_terms > 0 && (!x || !z || !coef)) return fail(PP_ERR_ARG, "null term arrays");
+  if ((uint64_t)n_terms >= (1ull << 31)) return fail(PP_ERR_ARG, "too many input terms");
+  PP_TRY(ensure_capacity(c, std::max<uint64_t>(4 * (uint64_t)n_terms, 1024)));
+  return ingest_terms(c, n_terms, x, z, coef, false, true);
+}
+
 pp_status pp_destroy(pp_ctx* c) {
   if (!c) return PP_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -1312,6 +1344,13 @@ pp_status pp_expect(pp_ctx* c, const double* bloch, double* out) {
   PP_CUDA(cudaStreamSynchronize(c->stream));
   memcpy(out, c->h_out, sizeof(double) * c->B);
   return PP_OK;
+}
+
+pp_status pp_expect_basis(pp_ctx* c, const uint8_t* bits, double* out) {
+  if (!c || !bits || !out) return fail(PP_ERR_ARG, "null argument");
+  std::vector<double> bloch((size_t)3 * c->n, 0.0);
+  for (int q = 0; q < c->n; ++q) bloch[3 * q + 2] = bits[q] ? -1.0 : 1.0;
+  return pp_expect(c, bloch.data(), out);
 }
 
 pp_status pp_num_terms(pp_ctx* c, int64_t* live, int64_t* stored) {
