@@ -434,6 +434,111 @@ def replica_throughput(dist, ms_total, e2e_ms, upd, device):
     return value, e2e_value, ms_max, e2e_max, total
 
 
+def _timed_run(pp, make, layers, boundary=True, bloch=None):
+    """Propagate through `layers` (packed gates, angles) on a fresh context
+    from make(); CUDA-event time of the whole run (creation included)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    prop = make()
+    for packed, th in layers:
+        pp.pp_apply_layer(prop.ctx, packed, th, boundary)
+    val = prop.expect(bloch) if bloch is not None else None
+    t1.record(stream)
+    torch.cuda.synchronize()
+    st = prop.stats()
+    live = prop.num_terms()[0]
+    prop.close()
+    return t0.elapsed_time(t1), st, live, val
+
+
+def bench_workload(args):
+    """The other workloads through the same C ABI, one JSON line each (one
+    GPU; not the headline).  a2a64: all-to-all Heisenberg n=64, 10 steps,
+    eps 1e-5, Neel, per-gate damping p=0.01, merged under S_64 and plain,
+    and the per-layer damping variant.  batched64: ring n=64, 256 angle sets
+    in [0, pi/2], eps 1e-5 any-column, the first three steps (the table grows
+    about tenfold per step), FP64 and FP32 rows, against the same 256 angle
+    sets run one column at a time.  xxz36: all-to-all XXZ n=36, dt 0.05,
+    S^2/S_0^2, |+>^n, eps 0.05, merged after each of the first 16 XX/YY/ZZ
+    sublayers."""
+    import torch
+    import paper_2512_12094_gb300 as pp
+    torch.cuda.set_device(0)
+    pp.build()
+    pp.load()
+
+    def packed_layers(wl, count=None):
+        L = len(wl.circuit.layers)
+        out = []
+        for k, layer in enumerate(reversed(range(L))):
+            if count is not None and k >= count:
+                break
+            gx, gz, th = wl.circuit.gate_arrays(layer)
+            out.append((pp.pack_gates(gx, gz), th))
+        return out
+
+    def line(name, ms, updates, extra):
+        d = {"metric": "pauli_term_gate_updates_per_s", "value": updates / (ms / 1e3),
+             "unit": "updates/s", "n_gpus": 1, "ms_per_run": ms, "higher_is_better": True,
+             "dtype": "f64", "data": "synthetic", "config": {"workload": name}}
+        d.update(extra)
+        print(json.dumps(d), flush=True)
+
+    names = args.workload.split(",")
+    if "a2a64" in names:
+        for label, group, mode in (("a2a64_S64_per_gate_noise", 2, 1), ("a2a64_plain_per_gate_noise", 0, 1),
+                                   ("a2a64_S64_per_layer_noise", 2, 2)):
+            wl = pi.config2_all_to_all()
+            wl.noise_mode = mode
+            layers = packed_layers(wl)
+            make = lambda: pp.Propagator.from_workload(wl, symmetry=group)  # noqa: E731
+            _timed_run(pp, make, layers[:1])  # warm-up
+            ms, st, live, val = _timed_run(pp, make, layers, bloch=wl.state.bloch)
+            line(label, ms, st["gate_updates"], {"result": {"expect": val, "live_terms": live},
+                                                 "gates_per_run": len(layers) * 6048})
+    if "batched64" in names:
+        n, B, steps = 64, 256, 3
+        angles = pi.batched_ring_angles(B, 0)
+        layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
+        gx, gz, _ = pi.Circuit(n, [layer]).gate_arrays(0)
+        th = np.zeros((3 * n, B))
+        th[:n], th[n:2 * n], th[2 * n:] = angles[:, 0], angles[:, 1], angles[:, 2]
+        x, z, c = pi.mean_z(n).arrays()
+        coef = np.repeat(c[:, None], B, axis=1)
+        packed = pp.pack_gates(gx, gz)
+        for f32 in (False, True):
+            make = lambda: pp.Propagator(n, x, z, coef, eps=1e-5, batch=B, f32=f32)  # noqa: E731
+            _timed_run(pp, make, [(packed, th)])
+            ms, st, live, _ = _timed_run(pp, make, [(packed, th)] * steps)
+            line("ring64_B256_%s_3steps" % ("fp32" if f32 else "fp64"), ms, st["gate_updates"] * B,
+                 {"unit_note": "column updates (live strings x gates x 256 columns)",
+                  "result": {"live_terms": live}})
+        # the same 256 angle sets, one single-column context each
+        total_ms, total_upd = 0.0, 0.0
+        for b in range(B):
+            thb = np.ascontiguousarray(th[:, b])
+            make = lambda: pp.Propagator(n, x, z, c, eps=1e-5)  # noqa: E731
+            if b == 0:
+                _timed_run(pp, make, [(packed, thb)])
+            ms, st, _, _ = _timed_run(pp, make, [(packed, thb)] * steps)
+            total_ms += ms
+            total_upd += st["gate_updates"]
+        line("ring64_256_columns_one_at_a_time_3steps", total_ms, total_upd,
+             {"unit_note": "column updates; each column truncated on its own"})
+    if "xxz36" in names:
+        wl = pi.xxz_all_to_all(36, 0.05, 6, eps=0.05, symmetry=2, split=True)
+        layers = packed_layers(wl, 16)
+        make = lambda: pp.Propagator.from_workload(wl, symmetry=2)  # noqa: E731
+        _timed_run(pp, make, layers[:3])
+        ms, st, live, val = _timed_run(pp, make, layers, bloch=wl.state.bloch)
+        line("xxz36_split_eps0.05_16_sublayers", ms, st["gate_updates"],
+             {"result": {"S2_over_S02": val, "live_terms": live}})
+
+
 def bench_reference(args):
     """The oracle as the reference arm, on the host cores (rank 0 only)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -469,10 +574,14 @@ def main():
                     help="serve N jobs of the scaled Poisson stream instead of the main job")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--workload", default="",
+                    help="comma list of a2a64, batched64, xxz36: time those workloads instead")
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     args = ap.parse_args()
-    if args.serving > 0:
+    if args.workload:
+        bench_workload(args)
+    elif args.serving > 0:
         bench_serving(args)
     elif args.profile_layer >= 0:
         profile_layer(args)
