@@ -441,7 +441,14 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
     __syncthreads();  // s_gate[buf] complete
     gate_pass<W>(t, ctl, s_gate[buf], T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
     if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);  // overlaps the barrier wait
-    if (!grid_sync(ctl, target, s_ok)) return;
+    if (gridDim.x == 1) {
+      // a small table in one block: its own writes and atomics, ordered by a
+      // fence and the block barrier, are all the next gate depends on
+      __threadfence();
+      __syncthreads();
+    } else if (!grid_sync(ctl, target, s_ok)) {
+      return;
+    }
     T0 += __ldcg(&ctl->cnt[slot]);
     L0 += __ldcg(&ctl->dlt[slot]);
     if (__ldcg(&ctl->error) != 0u) return;  // uniform after the barrier
