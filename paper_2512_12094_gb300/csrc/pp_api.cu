@@ -427,6 +427,37 @@ pp_status merge_active(pp_ctx* c, int group) {
   return PP_OK;
 }
 
+// The symmetry merge of a layer queued right behind its gates, before the
+// host knows whether they all ran: every step checks the layer's stall flag
+// on the device and does nothing if a gate stopped for capacity.  The host
+// reads the control block once afterwards (finish_queued_merge) instead of
+// once after the gates and once after the merge.
+pp_status queue_merge(pp_ctx* c, int group) {
+  const int dst = 1 - c->active;
+  Buf& d = c->buf[dst];
+  Buf& s = c->buf[c->active];
+  PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
+  PP_CUDA(launch_ctl_insert(c->stream, c->d_ctl, 0, 1));
+  const int grid = c->sms * 8;  // grid-stride; the count is on the device
+  PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid, c->stream, s.keys, s.coef, 0,
+                              &c->d_ctl->n_terms, c->cfg.coeff_eps > 0.0 ? 1 : 0, desc_of(c, d),
+                              c->d_ctl, 1));
+  PP_CUDA(launch_finalize(grid, c->stream, desc_of(c, d), c->d_ctl, c->cfg.coeff_eps, 1));
+  PP_CUDA(launch_ctl_commit(c->stream, c->d_ctl, 1));
+  c->launches += 4;
+  return PP_OK;
+}
+
+// After the control block was read and showed no stall: the queued merge ran.
+pp_status finish_queued_merge(pp_ctx* c) {
+  c->n_terms = c->h_ctl->n_terms;
+  c->n_live = c->h_ctl->n_live;
+  PP_TRY(activate(c, 1 - c->active));
+  c->merged = true;
+  c->merges++;
+  return PP_OK;
+}
+
 bool key_has_bits_beyond(const uint64_t* x, const uint64_t* z, int n, int W) {
   for (int j = 0; j < W; ++j) {
     int lo = 64 * j;
@@ -1078,6 +1109,10 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   }
   const GateArgs* d_args = nullptr;
   if (layered && !args.empty()) PP_TRY(device_args(c, args, &d_args));
+  // with a group (single column) the boundary merge is queued right behind the
+  // gates, guarded by the stall flag, so one read of the control block serves both
+  const bool queue_it = symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE && !c->batched;
+  bool merged_now = false;
   if (!args.empty()) {
     unsigned first = 0;
     for (;;) {
@@ -1093,6 +1128,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       }
       PP_CUDA(launch_chain_finish(c->stream, c->d_ctl, (unsigned)args.size()));
       c->launches += 2;
+      if (queue_it) PP_TRY(queue_merge(c, c->cfg.symmetry));
       PP_TRY(read_ctl(c));
       PP_TRY(check_device_error(c));
       const unsigned end = c->h_ctl->stall ? c->h_ctl->stall - 1u : (unsigned)args.size();
@@ -1106,16 +1142,29 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       } else {
         PP_TRY(collect_gate_times(c, first, end));
       }
+      if (!c->h_ctl->stall) {
+        // stored entries after the last gate: its slot (a merge leaves the slots)
+        const int q = (int)((args.size() + 2u) % 3u);
+        const uint64_t after = c->h_ctl->base[q] + c->h_ctl->cnt[q];
+        c->last_growth = (double)after / (double)n_start;
+        if (queue_it) {
+          PP_TRY(finish_queued_merge(c));
+          merged_now = true;
+        } else {
+          c->n_terms = c->h_ctl->n_terms;
+          c->n_live = c->h_ctl->n_live;
+        }
+        break;
+      }
+      // gate `end` found too little room (the queued merge did nothing):
+      // compact and grow, then resume there
       c->n_terms = c->h_ctl->n_terms;
       c->n_live = c->h_ctl->n_live;
-      if (!c->h_ctl->stall) break;
-      // gate `end` found too little room: compact and grow, then resume there
       PP_TRY(make_room(c, std::max<uint64_t>(factor, 4)));
       first = end;
     }
-    c->last_growth = (double)c->n_terms / (double)n_start;
   }
-  if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE) {
+  if (symmetric_boundary && c->cfg.symmetry != PP_SYM_NONE && !merged_now) {
     PP_TRY(merge_active(c, c->cfg.symmetry));
   }
   return PP_OK;

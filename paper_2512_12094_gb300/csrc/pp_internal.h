@@ -104,7 +104,10 @@ struct OverlapArgs {
 cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate);
 // Before a merge or compaction into a fresh table: append cursor n_next <-
 // first_free, live count <- 0 (stream ordered, no host round trip).
-cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free);
+cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free,
+                              int guarded = 0);
+// n_terms <- n_next (after a merge or compaction); guarded as above.
+cudaError_t launch_ctl_commit(cudaStream_t s, DevCtl* ctl, int guarded);
 // After the gates of a layer (n_gates of them): (n_terms, n_live) <- the state
 // after the last gate that ran.
 cudaError_t launch_chain_finish(cudaStream_t s, DevCtl* ctl, unsigned n_gates);
@@ -128,11 +131,13 @@ cudaError_t launch_gate(int W, int grid, cudaStream_t s, const DevTable* tab, De
 cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cudaStream_t s,
                                 const uint64_t* src_keys, const double* src_coef,
                                 uint64_t count, const unsigned long long* count_dev,
-                                int skip_zero, DevTable dst, DevCtl* ctl);
+                                int skip_zero, DevTable dst, DevCtl* ctl, int guarded = 0);
 
 // Coefficient truncation (eps > 0) of dst entries [0, ctl->n_next); adds the
-// live count to ctl->n_live.
-cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps);
+// live count to ctl->n_live.  guarded: do nothing if ctl->stall is set (a
+// merge queued behind a layer that may have stopped for capacity).
+cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps,
+                            int guarded = 0);
 
 // Copy entries of src[0, count) that are kept (not truncated under eps, and
 // |c| >= extra_eps when extra_eps > 0, weight <= extra_wmax when >= 0) into

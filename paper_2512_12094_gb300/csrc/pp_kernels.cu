@@ -455,9 +455,15 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
   }
 }
 
-__global__ void ctl_insert_kernel(DevCtl* ctl, unsigned long long first_free) {
+__global__ void ctl_insert_kernel(DevCtl* ctl, unsigned long long first_free, int guarded) {
+  if (guarded && ctl->stall != 0u) return;
   ctl->n_next = first_free;
   ctl->n_live = 0;
+}
+
+__global__ void ctl_commit_kernel(DevCtl* ctl, int guarded) {
+  if (guarded && ctl->stall != 0u) return;
+  ctl->n_terms = ctl->n_next;
 }
 
 __global__ void chain_init_kernel(DevCtl* ctl, unsigned first_gate) {
@@ -486,7 +492,10 @@ template <int W, int G>
 __global__ void __launch_bounds__(kBlock)
     merge_insert_kernel(const uint64_t* __restrict__ src_keys, const double* __restrict__ src_coef,
                         uint64_t count, const unsigned long long* count_dev, int skip_zero,
-                        int wmax, int n, int lx, DevTable dst, DevCtl* ctl) {
+                        int wmax, int n, int lx, DevTable dst, DevCtl* ctl, int guarded) {
+  // guarded: queued behind a layer before its outcome is known; nothing to
+  // do if that layer stopped for capacity
+  if (guarded && *reinterpret_cast<volatile unsigned*>(&ctl->stall) != 0u) return;
   const uint64_t T = count_dev ? *count_dev : count;
   unsigned err = 0;
   unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
@@ -552,8 +561,10 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // Coefficient truncation of the merged entries and live count.
-__global__ void __launch_bounds__(kBlock) finalize_kernel(DevTable t, DevCtl* ctl, double eps) {
+__global__ void __launch_bounds__(kBlock) finalize_kernel(DevTable t, DevCtl* ctl, double eps,
+                                                         int guarded) {
   __shared__ long long s_live[kBlock / 32];
+  if (guarded && *reinterpret_cast<volatile unsigned*>(&ctl->stall) != 0u) return;
   const uint64_t T = *reinterpret_cast<volatile unsigned long long*>(&ctl->n_next);
   long long live = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -789,8 +800,14 @@ __global__ void __launch_bounds__(kBlock)
     default: return cudaErrorInvalidValue;        \
   }
 
-cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free) {
-  ctl_insert_kernel<<<1, 1, 0, s>>>(ctl, first_free);
+cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free,
+                              int guarded) {
+  ctl_insert_kernel<<<1, 1, 0, s>>>(ctl, first_free, guarded);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctl_commit(cudaStream_t s, DevCtl* ctl, int guarded) {
+  ctl_commit_kernel<<<1, 1, 0, s>>>(ctl, guarded);
   return cudaGetLastError();
 }
 
@@ -873,11 +890,11 @@ cudaError_t launch_gate(int W, int grid, cudaStream_t s, const DevTable* tab, De
 cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cudaStream_t s,
                                   const uint64_t* src_keys, const double* src_coef,
                                   uint64_t count, const unsigned long long* count_dev,
-                                  int skip_zero, DevTable dst, DevCtl* ctl) {
+                                  int skip_zero, DevTable dst, DevCtl* ctl, int guarded) {
   const int lx = group >> 8;  // group code: kind | (torus width << 8)
 #define PP_MERGE_G(GG)                                                                     \
   PP_DISPATCH_W(W, (merge_insert_kernel<WW, GG><<<grid, kBlock, 0, s>>>(                   \
-                       src_keys, src_coef, count, count_dev, skip_zero, wmax, n, lx, dst, ctl)))
+                       src_keys, src_coef, count, count_dev, skip_zero, wmax, n, lx, dst, ctl, guarded)))
   switch (group & 0xFF) {
     case 0: PP_MERGE_G(0); break;
     case 1: PP_MERGE_G(1); break;
@@ -891,8 +908,9 @@ cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps) {
-  finalize_kernel<<<grid, kBlock, 0, s>>>(dst, ctl, eps);
+cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps,
+                            int guarded) {
+  finalize_kernel<<<grid, kBlock, 0, s>>>(dst, ctl, eps, guarded);
   return cudaGetLastError();
 }
 
