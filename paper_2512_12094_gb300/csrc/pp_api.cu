@@ -652,51 +652,57 @@ pp_status ingest_terms(pp_ctx* c, int64_t n_terms, const uint64_t* x, const uint
   if (n_terms > 0) {
     uint64_t* d_keys = nullptr;
     double* d_coef = nullptr;
-    unsigned* d_bad = nullptr;
-    if ((st = dmalloc(c, (void**)&d_keys, (size_t)n_terms * 16 * W)) != PP_OK ||
-        (st = dmalloc(c, (void**)&d_coef, hc.size() * 8)) != PP_OK)
-      return st;
+    double* acc = nullptr;
+    const size_t key_bytes = (size_t)n_terms * 16 * W, coef_bytes = hc.size() * 8;
+    const size_t acc_bytes = c->batched ? (size_t)n_terms * c->B * sizeof(double) : 0;
+    // the staging buffers go back to the pool on every exit
+    auto release = [&](pp_status r) {
+      dfree(c, d_keys, key_bytes);
+      dfree(c, d_coef, coef_bytes);
+      dfree(c, acc, acc_bytes);
+      return r;
+    };
+    if ((st = dmalloc(c, (void**)&d_keys, key_bytes)) != PP_OK ||
+        (st = dmalloc(c, (void**)&d_coef, coef_bytes)) != PP_OK ||
+        (c->batched && (st = dmalloc(c, (void**)&acc, acc_bytes)) != PP_OK))
+      return release(st);
     std::vector<uint64_t> packed((size_t)n_terms * 2 * W);
     for (int64_t i = 0; i < n_terms; ++i)
       for (int j = 0; j < W; ++j) {
         packed[i * 2 * W + j] = hx[i * W + j];
         packed[i * 2 * W + W + j] = hz[i * W + j];
       }
-    (void)d_bad;
     if (cudaMemcpyAsync(d_keys, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(d_coef, hc.data(), hc.size() * 8, cudaMemcpyHostToDevice, c->stream) !=
+        cudaMemcpyAsync(d_coef, hc.data(), coef_bytes, cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess)
-      return fail(PP_ERR_CUDA, "term upload failed");
-    if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return st;
+      return release(fail(PP_ERR_CUDA, "term upload failed"));
+    if ((st = ctl_prepare_insert(c, 0)) != PP_OK) return release(st);
     cudaError_t e;
     if (c->batched) {
-      double* acc = nullptr;
-      const size_t acc_bytes = (size_t)n_terms * c->B * sizeof(double);
-      if ((st = dmalloc(c, (void**)&acc, acc_bytes)) != PP_OK) return st;
       e = cudaMemsetAsync(acc, 0, acc_bytes, c->stream);
       if (e == cudaSuccess)
         e = launch_merge_batched(W, c->cfg.symmetry, c->n, c->cfg.max_weight, 0,
                                  grid_for(c, n_terms, 32), c->stream, d_keys, d_coef, nullptr,
                                  (uint64_t)n_terms, desc_of(c, c->buf[c->active]), acc, c->d_ctl);
       if (e == cudaSuccess)
-        e = launch_finalize_batched(grid_for(c, n_terms, 32), c->stream, desc_of(c, c->buf[c->active]),
-                                    acc, c->d_ctl, c->cfg.coeff_eps);
-      if (e != cudaSuccess) return cuda_fail(e, "batched ingest");
-      if ((st = ctl_commit(c)) != PP_OK) return st;
-      dfree(c, acc, acc_bytes);
+        e = launch_finalize_batched(grid_for(c, n_terms, 32), c->stream,
+                                    desc_of(c, c->buf[c->active]), acc, c->d_ctl,
+                                    c->cfg.coeff_eps);
+      if (e != cudaSuccess) return release(cuda_fail(e, "batched ingest"));
     } else {
       e = launch_merge_insert(W, c->cfg.symmetry, c->n, c->cfg.max_weight, grid_for(c, n_terms, 4),
                               c->stream, d_keys, d_coef, (uint64_t)n_terms, nullptr, 0,
                               desc_of(c, c->buf[c->active]), c->d_ctl);
-      if (e != cudaSuccess) return cuda_fail(e, "merge_insert");
-      e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c, c->buf[c->active]), c->d_ctl,
-                          c->cfg.coeff_eps);
-      if (e != cudaSuccess) return cuda_fail(e, "finalize");
-      if ((st = ctl_commit(c)) != PP_OK) return st;
+      if (e == cudaSuccess)
+        e = launch_finalize(grid_for(c, n_terms, 4), c->stream, desc_of(c, c->buf[c->active]),
+                            c->d_ctl, c->cfg.coeff_eps);
+      if (e != cudaSuccess) return release(cuda_fail(e, "ingest merge"));
     }
-    dfree(c, d_keys, (size_t)n_terms * 16 * W);
-    dfree(c, d_coef, hc.size() * 8);
+    // the packed host copy is read by the upload above: keep it until the
+    // stream has passed it (ctl_commit synchronises)
+    if ((st = ctl_commit(c)) != PP_OK) return release(st);
+    release(PP_OK);
   }
   c->merged = true;
   return PP_OK;

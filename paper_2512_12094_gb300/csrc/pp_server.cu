@@ -113,7 +113,7 @@ pp_status run_job(const Job& j, cudaStream_t stream, pp_job_result& r) {
 void worker_main(pp_server* s) {
   cudaSetDevice(s->device);
   cudaStream_t stream = nullptr;
-  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  const bool have_stream = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
   for (;;) {
     std::unique_ptr<Job> j;
     {
@@ -126,7 +126,12 @@ void worker_main(pp_server* s) {
     j->t_start = Clock::now();
     pp_job_result r;
     memset(&r, 0, sizeof(r));
-    pp_status st = run_job(*j, stream, r);
+    pp_status st = PP_ERR_CUDA;
+    if (have_stream) {
+      st = run_job(*j, stream, r);
+    } else {
+      snprintf(r.message, sizeof(r.message), "%s", "the worker could not create its CUDA stream");
+    }
     const auto t_end = Clock::now();
     std::unique_lock<std::mutex> lock(s->mu);
     s->reserved -= j->reserve;
@@ -148,7 +153,7 @@ void worker_main(pp_server* s) {
     }
     s->cv_work.notify_all();
   }
-  cudaStreamDestroy(stream);
+  if (have_stream) cudaStreamDestroy(stream);
 }
 
 }  // namespace
