@@ -461,8 +461,8 @@ def bench_workload(args):
     eps 1e-5, Neel, per-gate damping p=0.01, merged under S_64 and plain,
     and the per-layer damping variant.  batched64: ring n=64, 256 angle sets
     in [0, pi/2], eps 1e-5 any-column, the first three steps (the table grows
-    about tenfold per step), FP64 and FP32 rows, against the same 256 angle
-    sets run one column at a time.  xxz36: all-to-all XXZ n=36, dt 0.05,
+    about tenfold per step), FP64 and FP32 rows; columns64: the same 256
+    angle sets run one column at a time.  xxz36: all-to-all XXZ n=36, dt 0.05,
     S^2/S_0^2, |+>^n, eps 0.05, merged after each of the first 16 XX/YY/ZZ
     sublayers."""
     import torch
@@ -500,7 +500,7 @@ def bench_workload(args):
             ms, st, live, val = _timed_run(pp, make, layers, bloch=wl.state.bloch)
             line(label, ms, st["gate_updates"], {"result": {"expect": val, "live_terms": live},
                                                  "gates_per_run": len(layers) * 6048})
-    if "batched64" in names:
+    if "batched64" in names or "columns64" in names:
         n, B, steps = 64, 256, 3
         angles = pi.batched_ring_angles(B, 0)
         layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
@@ -510,7 +510,7 @@ def bench_workload(args):
         x, z, c = pi.mean_z(n).arrays()
         coef = np.repeat(c[:, None], B, axis=1)
         packed = pp.pack_gates(gx, gz)
-        for f32 in (False, True):
+        for f32 in ((False, True) if "batched64" in names else ()):
             make = lambda: pp.Propagator(n, x, z, coef, eps=1e-5, batch=B, f32=f32)  # noqa: E731
             _timed_run(pp, make, [(packed, th)])
             ms, st, live, _ = _timed_run(pp, make, [(packed, th)] * steps)
@@ -519,7 +519,7 @@ def bench_workload(args):
                   "result": {"live_terms": live}})
         # the same 256 angle sets, one single-column context each
         total_ms, total_upd = 0.0, 0.0
-        for b in range(B):
+        for b in (range(B) if "columns64" in names else ()):
             thb = np.ascontiguousarray(th[:, b])
             make = lambda: pp.Propagator(n, x, z, c, eps=1e-5)  # noqa: E731
             if b == 0:
@@ -527,8 +527,9 @@ def bench_workload(args):
             ms, st, _, _ = _timed_run(pp, make, [(packed, thb)] * steps)
             total_ms += ms
             total_upd += st["gate_updates"]
-        line("ring64_256_columns_one_at_a_time_3steps", total_ms, total_upd,
-             {"unit_note": "column updates; each column truncated on its own"})
+        if "columns64" in names:
+            line("ring64_256_columns_one_at_a_time_3steps", total_ms, total_upd,
+                 {"unit_note": "column updates; each column truncated on its own"})
     if "xxz36" in names:
         wl = pi.xxz_all_to_all(36, 0.05, 6, eps=0.05, symmetry=2, split=True)
         layers = packed_layers(wl, 16)
@@ -575,7 +576,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--workload", default="",
-                    help="comma list of a2a64, batched64, xxz36: time those workloads instead")
+                    help="comma list of a2a64, batched64, columns64, xxz36: time those instead")
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     args = ap.parse_args()

@@ -1109,9 +1109,11 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
     const uint64_t want = (est + kBlock - 1) / kBlock;
     grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
   } else {
-    // a power of two so that captured graphs are reused
-    while ((uint64_t)grid_b * kBlock < est) grid_b <<= 1;
-    grid_b = std::min(grid_b, c->sms * c->gate_bps);
+    // a power of two so that captured graphs are reused; batched rows take
+    // a warp B/32 steps per pair, so they get B/32 times the blocks
+    const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
+    while ((uint64_t)grid_b * kBlock < est * rowf) grid_b <<= 1;
+    grid_b = std::min(grid_b, c->sms * (c->batched ? 8 : c->gate_bps));
   }
   const GateArgs* d_args = nullptr;
   if (layered && !args.empty()) PP_TRY(device_args(c, args, &d_args));
