@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
   __shared__ long long s_delta[kWarps];
   __shared__ unsigned long long s_ac[kWarps];
   __shared__ unsigned s_err;
+  __shared__ T s_cs[2 * 512];  // this gate's cos[0, B), sin[B, 2B) (B <= 512)
   const unsigned gid = g.gate_id;
   const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -86,7 +87,10 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = t.B;
   T* rows = static_cast<T*>(t.rows);
-  const T* cs = static_cast<const T*>(g.csb);  // cos[0, B), sin[B, 2B)
+  // cos and sin of every column, read by every action: staged once per block
+  for (int k = threadIdx.x; k < 2 * B; k += kBlock) s_cs[k] = static_cast<const T*>(g.csb)[k];
+  __syncthreads();
+  const T* cs = s_cs;
   const bool noise = g.damp != nullptr;
   const bool use_eps = g.use_eps != 0;
   const uint64_t eb = use_eps ? eps_bits_of<T>(g.eps) : 0ull;
@@ -162,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
       T* rq = rows + ii * B;
       bool anyQ = false, anyR = false;
       if (a == 1) {
+        #pragma unroll 4
         for (int col = lane; col < B; col += 32) {
           const T v = mul_rn(ld_row(rq + col), fq);
           rq[col] = v;
@@ -169,6 +174,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         }
       } else if (a == 2) {
         T* rr = rows + (uint64_t)jj * B;
+        #pragma unroll 4
         for (int col = lane; col < B; col += 32) {
           T dq = aQ ? ld_row(rq + col) : (T)0, dr = aR ? ld_row(rr + col) : (T)0;
           if (kqq) dq = mul_rn(dq, fq);
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         }
       } else {
         // first pass: which of Q's new row and the child row survive
+        #pragma unroll 4
         for (int col = lane; col < B; col += 32) {
           T dq = ld_row(rq + col);
           if (kqq) dq = mul_rn(dq, fq);
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         }
         const bool write_child = birth && idx < t.cap;
         T* rn = rows + idx * B;
+        #pragma unroll 4
         for (int col = lane; col < B; col += 32) {
           T dq = ld_row(rq + col);
           if (kqq) dq = mul_rn(dq, fq);
