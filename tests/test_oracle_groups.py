@@ -191,3 +191,35 @@ def test_theorem1_torus_merge_is_exact(oracle_lib, lx, ly):
     wl.state = pi.zero_state(n)
     _, plain = oracle_lib.run_workload(wl, group=0, record_each_step=True)
     np.testing.assert_allclose(plain, ref, atol=1e-10, rtol=0)
+
+
+# ------------------------------------------------- XXZ workload (total spin)
+
+@pytest.mark.parametrize("split", [True, False])
+def test_xxz_total_spin_against_statevector_and_conservation(oracle_lib, split):
+    """All-to-all XXZ with alpha = 0: H = -J (2 S^2 + 2 Delta S_z^2) + const.
+
+    Split into XX / YY / ZZ sublayers each step is exp(-i t S_a^2) up to a
+    phase: every sublayer is a product of commuting gates that S_n maps onto
+    itself, so merging after it is exact (Theorem 1), and each commutes with
+    S^2, so without truncation <S^2>/S_0^2 stays exactly 1.
+
+    In the pair-by-pair order (pairs outer, XX YY ZZ inner) the gate multiset
+    is S_n-invariant but the ordered product of non-commuting pair gates is
+    not, so merging after the layer is exact only up to Trotter error.  The
+    paper merges after such layers too; the pin records that the merged value
+    then differs from the plain one, while the plain one matches the state
+    vector and drifts from 1 by Trotter error."""
+    n = 6
+    wl = pi.xxz_all_to_all(n, 0.1, 3, eps=0.0, symmetry=2, split=split)
+    plain_st, plain = oracle_lib.run_workload(wl, group=0, record_each_step=True)
+    merged_st, merged = oracle_lib.run_workload(wl, group=2, record_each_step=True)
+    ref = sv.statevector_expectations(wl.circuit.layers, wl.observable.terms, wl.state.bloch)
+    np.testing.assert_allclose(plain, ref, atol=1e-10, rtol=0)
+    assert len(merged_st) < len(plain_st)
+    if split:
+        np.testing.assert_allclose(merged, plain, atol=1e-12, rtol=0)
+        np.testing.assert_allclose(plain, 1.0, atol=1e-12, rtol=0)
+    else:
+        assert max(abs(v - 1.0) for v in plain) > 1e-3
+        assert max(abs(a - b) for a, b in zip(merged, plain)) > 1e-3
