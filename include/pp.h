@@ -26,7 +26,9 @@
  * Threads: a pp_ctx is used by one host thread at a time.
  * Memory: host pointers passed in are read before the call returns and are
  *   never retained.  Device memory of a context is owned by the context and
- *   released by pp_destroy.
+ *   comes from the library's stream-ordered memory pool (one per device);
+ *   pp_destroy returns it to that pool, which keeps it mapped for later
+ *   contexts until the process exits.
  */
 #ifndef PP_H
 #define PP_H
@@ -168,6 +170,10 @@ pp_status pp_destroy(pp_ctx* ctx);
  * layer ends with the symmetry merge of Eq. (O-merging) (Algorithm 2 for
  * Z_n, Algorithm 3 for S_n) and another truncation.  Callers apply layers
  * from the last (l = L) to the first (l = 1).
+ * The merge is exact (Theorem 1) when the layer's unitary commutes with the
+ * group, e.g. a product of commuting sublayers each mapped onto itself; the
+ * check below tests the multiset only, so for an ordered product of
+ * non-commuting gates the merge holds up to the ordering (Trotter) error.
  * Errors: PP_ERR_ARG; PP_ERR_SYMMETRY when check_symmetry is set and the gate
  * multiset (with angles) is not mapped onto itself by the group generators;
  * PP_ERR_CAPACITY when the table would exceed mem_budget_bytes -- the context
