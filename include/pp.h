@@ -123,6 +123,7 @@ typedef struct {
   double gate_kernel_ms;   /* with profile_kernels: summed duration of the kernels that applied
                               gates (one per layer, or one per gate without layer_kernel) */
   int64_t gate_kernels_timed; /* number of launches summed in gate_kernel_ms */
+  double grid_scale;       /* blocks per gate pass relative to the default sizing (pp_tune) */
 } pp_stats_t;
 
 /* Fill *cfg with defaults: n_qubits = 0 (must be set), no symmetry, batch 1,
@@ -159,6 +160,18 @@ pp_status pp_import(pp_ctx* ctx, int64_t n_terms, const uint64_t* x, const uint6
 
 /* Release every device and host resource of ctx.  NULL is accepted. */
 pp_status pp_destroy(pp_ctx* ctx);
+
+/* Autotuning (an implementation facility; the paper has no counterpart).
+ * Times one application of the layer (gates in time order, theta [n_gates][batch],
+ * as for pp_apply_layer, without the boundary merge) on a copy of the context's
+ * current table for each candidate launch size -- 0.5, 1, 2 and 4 times the
+ * default number of blocks per gate pass -- puts the table and the statistics
+ * back after each trial, and keeps the fastest size for the context's later
+ * layers (pp_stats_t.grid_scale; *chosen_scale when not NULL).  Results of
+ * later calls do not depend on the choice.  An empty table leaves the setting
+ * as it is.  Errors: as pp_apply_layer (the table is restored). */
+pp_status pp_tune(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const double* theta,
+                  double* chosen_scale);
 
 /* One Heisenberg layer O_{l-1} = U_l^dag O~_l U_l (Algorithm 1, step 2a, and
  * Appendix A).  gates[0..n_gates) and theta[n_gates][batch] describe U_l in TIME

@@ -121,7 +121,7 @@ class pp_stats_t(ctypes.Structure):
                 ("compactions", ctypes.c_int64), ("regrows", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("anticommuting_terms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("gate_kernel_ms", ctypes.c_double),
-                ("gate_kernels_timed", ctypes.c_int64)]
+                ("gate_kernels_timed", ctypes.c_int64), ("grid_scale", ctypes.c_double)]
 
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -143,6 +143,7 @@ _SIGS = {
     "pp_expect": [_vp, _vp, _f64p],
     "pp_expect_basis": [_vp, _vp, _f64p],
     "pp_import": [_vp, ctypes.c_int64, _vp, _vp, _vp],
+    "pp_tune": [_vp, ctypes.c_int, _vp, _vp, _f64p],
     "pp_num_terms": [_vp, _i64p, _i64p],
     "pp_export": [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64p],
     "pp_stats": [_vp, ctypes.POINTER(pp_stats_t)],
@@ -291,6 +292,16 @@ def pp_import(ctx, n_qubits: int, x, z, coef, batch: int = 1):
     z = np.ascontiguousarray(np.asarray(z, dtype=np.uint64).reshape(-1, W))
     c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, batch))
     _check(load().pp_import(ctx, c.shape[0], _ptr(x), _ptr(z), _ptr(c)))
+
+
+def pp_tune(ctx, packed_gates, theta) -> float:
+    """Time the layer at each candidate launch size on a copy of the table and
+    keep the fastest; returns the chosen scale."""
+    g = np.ascontiguousarray(packed_gates)
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    out = ctypes.c_double(0.0)
+    _check(load().pp_tune(ctx, g.shape[0], _ptr(g), _ptr(th), ctypes.byref(out)))
+    return out.value
 
 
 def pp_num_terms(ctx):

@@ -139,6 +139,7 @@ struct pp_ctx {
   int64_t launches = 0;
   std::vector<cudaEvent_t> ev_start, ev_end;  // per gate position (profile_kernels)
   double last_growth = 2.0;  // stored entries after / before the gates of the last layer
+  double grid_scale = 1.0;   // blocks per launch relative to the default sizing (pp_tune)
   double gate_ms = 0.0;
   int64_t gates_timed = 0;
 };
@@ -1031,7 +1032,7 @@ pp_status take_snapshot(pp_ctx* c, Buf& s, uint64_t n) {
   s = Buf();
   if (n == 0) return PP_OK;
   const size_t need = (size_t)n * (16 * c->W + c->row_bytes());
-  if (c->bytes + need > c->cfg.mem_budget_bytes)
+  if (c->cfg.mem_budget_bytes && c->bytes + need > c->cfg.mem_budget_bytes)
     return fail(PP_ERR_CAPACITY, "no room in the memory budget for the copy that lets a layer be undone");
   const Buf& a = c->buf[c->active];
   PP_TRY(dmalloc(c, (void**)&s.keys, (size_t)n * 16 * c->W));
@@ -1106,13 +1107,13 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   if (layered) {
     // persistent: one string per thread per pass, never more blocks than can
     // be co-resident (the grid barrier needs all of them)
-    const uint64_t want = (est + kBlock - 1) / kBlock;
+    const uint64_t want = (uint64_t)std::ceil((double)est * c->grid_scale / kBlock);
     grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
   } else {
     // a power of two so that captured graphs are reused; batched rows take
     // a warp B/32 steps per pair, so they get B/32 times the blocks
     const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
-    while ((uint64_t)grid_b * kBlock < est * rowf) grid_b <<= 1;
+    while ((double)grid_b * kBlock < (double)(est * rowf) * c->grid_scale) grid_b <<= 1;
     grid_b = std::min(grid_b, c->sms * (c->batched ? 8 : c->gate_bps));
   }
   const GateArgs* d_args = nullptr;
@@ -1319,6 +1320,85 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
   return st;
 }
 
+pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
+                  double* chosen_scale) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (n_gates < 0 || (n_gates > 0 && (!gates || !theta)))
+    return fail(PP_ERR_ARG, "bad gate arrays");
+  std::vector<GateArgs> args;
+  std::vector<int> src_t;
+  PP_TRY(build_gates(c, n_gates, gates, theta, args, src_t));
+  PP_TRY(ensure_merged(c));
+  if (c->n_terms == 0 || args.empty()) {  // nothing to time
+    if (chosen_scale) *chosen_scale = c->grid_scale;
+    return PP_OK;
+  }
+  // the table, the device statistics and the host counters, put back after every trial
+  Buf snap;
+  const uint64_t n0 = c->n_terms;
+  {
+    const pp_status ts = take_snapshot(c, snap, n0);
+    if (ts != PP_OK) {
+      free_snapshot(c, snap, n0);
+      return ts;
+    }
+  }
+  PP_TRY(read_ctl(c));
+  struct Counters {
+    double updates;
+    unsigned long long gates_done, ac_total;
+  } saved = {c->h_ctl->updates, c->h_ctl->gates_done, c->h_ctl->ac_total};
+  static_assert(offsetof(DevCtl, ac_total) - offsetof(DevCtl, updates) == 16,
+                "statistics counters are contiguous");
+  const int64_t launches = c->launches, merges = c->merges, compactions = c->compactions,
+                regrows = c->regrows, timed = c->gates_timed;
+  const double gate_ms = c->gate_ms, growth = c->last_growth;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto finish = [&](pp_status st) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    free_snapshot(c, snap, n0);
+    return st;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return finish(fail(PP_ERR_CUDA, "event creation failed"));
+  const double candidates[] = {0.5, 1.0, 2.0, 4.0};
+  double best_scale = c->grid_scale, best_ms = 1e300;
+  for (double scale : candidates) {
+    c->grid_scale = scale;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess)
+      return finish(fail(PP_ERR_CUDA, "event record failed"));
+    pp_status st = apply_layer_core(c, args, src_t, theta, 0);
+    if (st != PP_OK) {
+      restore_snapshot(c, snap, n0);
+      c->grid_scale = best_ms < 1e300 ? best_scale : 1.0;
+      return finish(st);
+    }
+    float ms = 0.f;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return finish(fail(PP_ERR_CUDA, "timing a trial failed"));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_scale = scale;
+    }
+    const pp_status rs = restore_snapshot(c, snap, n0);
+    if (rs != PP_OK) return finish(rs);
+  }
+  c->grid_scale = best_scale;
+  if (upload(c, &c->d_ctl->updates, &saved, sizeof(saved)) != cudaSuccess)
+    return finish(fail(PP_ERR_CUDA, "restoring statistics failed"));
+  c->launches = launches;
+  c->merges = merges;
+  c->compactions = compactions;
+  c->regrows = regrows;
+  c->gates_timed = timed;
+  c->gate_ms = gate_ms;
+  c->last_growth = growth;
+  if (chosen_scale) *chosen_scale = best_scale;
+  return finish(PP_OK);
+}
+
 pp_status pp_canonicalize(pp_ctx* c) {
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (c->cfg.symmetry == PP_SYM_NONE) return fail(PP_ERR_STATE, "context has no symmetry");
@@ -1493,6 +1573,7 @@ pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
   out->kernel_launches = c->launches;
   out->gate_kernel_ms = c->gate_ms;
   out->gate_kernels_timed = c->gates_timed;
+  out->grid_scale = c->grid_scale;
   return PP_OK;
 }
 
