@@ -462,7 +462,8 @@ def bench_workload(args):
     and the per-layer damping variant.  batched64: ring n=64, 256 angle sets
     in [0, pi/2], eps 1e-5 any-column, the first three steps (the table grows
     about tenfold per step), FP64 and FP32 rows; columns64: the same 256
-    angle sets run one column at a time.  xxz36: all-to-all XXZ n=36, dt 0.05,
+    angle sets run one column at a time.  canon64: representatives of 2^24
+    random n=64 strings under Z_64, D_64 and S_64 (pp_canonical_keys).  xxz36: all-to-all XXZ n=36, dt 0.05,
     S^2/S_0^2, |+>^n, eps 0.05, merged after each of the first 16 XX/YY/ZZ
     sublayers."""
     import torch
@@ -530,6 +531,32 @@ def bench_workload(args):
         if "columns64" in names:
             line("ring64_256_columns_one_at_a_time_3steps", total_ms, total_upd,
                  {"unit_note": "column updates; each column truncated on its own"})
+    if "canon64" in names:
+        # representatives of 2^24 random n=64 strings (16 B each), resident in HBM:
+        # 512 MB read + written per call, far above L2
+        m, n = 1 << 24, 64
+        rng = np.random.default_rng(3)
+        keys = torch.from_numpy(rng.integers(0, 2 ** 63, size=(m, 2), dtype=np.int64)).cuda()
+        out = torch.empty_like(keys)
+        hbm, kind = peaks()
+        for label, code in (("Z64", pp.SYM_ZN), ("D64", pp.SYM_DN), ("S64", pp.SYM_SN)):
+            pp.pp_canonical_keys(n, code, m, keys, out)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(5):
+                pp.pp_canonical_keys(n, code, m, keys, out)
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / 5
+            gbs = 2 * 16 * m / (ms / 1e3) / 1e9
+            print(json.dumps({"metric": "canonical_keys_per_s", "value": m / (ms / 1e3),
+                              "unit": "keys/s", "n_gpus": 1, "ms_per_call": ms,
+                              "higher_is_better": True, "data": "synthetic",
+                              "config": {"workload": "canonical_keys_n64_%s_16M" % label},
+                              "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                                      "peak_kind": kind}}), flush=True)
     if "xxz36" in names:
         wl = pi.xxz_all_to_all(36, 0.05, 6, eps=0.05, symmetry=2, split=True)
         layers = packed_layers(wl, 16)
@@ -576,7 +603,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--workload", default="",
-                    help="comma list of a2a64, batched64, columns64, xxz36: time those instead")
+                    help="comma list of a2a64, batched64, columns64, xxz36, canon64: time those")
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     args = ap.parse_args()
