@@ -53,7 +53,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -67,7 +67,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -204,7 +204,6 @@ def bench_ours(args):
                 ac += st["anticommuting_terms"]
                 gate_ms += st["gate_kernel_ms"]
                 gate_n += st["gate_kernels_timed"]
-        clk = clocks.stop()
         barrier()
         # end to end through the host-buffer API (inputs copied in, result read back)
         e2e_ms = 0.0
@@ -212,6 +211,7 @@ def bench_ours(args):
             for _ in range(args.steps):
                 _, _, ev = timed_job(True, False)
                 e2e_ms += ev[0].elapsed_time(ev[2])
+        clk = clocks.stop()  # both timed regions
     pupd = upd
 
     value, e2e_value, ms_max, e2e_max, total_upd = replica_throughput(dist, ms_total, e2e_ms, upd,
@@ -591,7 +591,7 @@ def bench_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
