@@ -167,9 +167,11 @@ pp_status pp_destroy(pp_ctx* ctx);
  * current table for each candidate launch size -- 0.5, 1, 2 and 4 times the
  * default number of blocks per gate pass -- puts the table and the statistics
  * back after each trial, and keeps the fastest size for the context's later
- * layers (pp_stats_t.grid_scale; *chosen_scale when not NULL).  Results of
- * later calls do not depend on the choice.  An empty table leaves the setting
- * as it is.  Errors: as pp_apply_layer (the table is restored). */
+ * layers (pp_stats_t.grid_scale; *chosen_scale when not NULL).  The terms
+ * and coefficients that later calls produce do not depend on the choice; the
+ * order of table entries may (merge sums use FP64 atomics, whose rounding
+ * order is never fixed).  An empty table leaves the setting as it is.
+ * Errors: as pp_apply_layer (the table is restored). */
 pp_status pp_tune(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const double* theta,
                   double* chosen_scale);
 
