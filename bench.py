@@ -39,8 +39,8 @@ KEY_BYTES = 16   # one uint64 X word + one uint64 Z word (n = 32)
 COEF_BYTES = 8   # FP64
 # DRAM bytes (read + write) per algorithmic byte of layer_kernel<1>, from the
 # ncu capture of one full layer of this workload summarised in
-# profiles/layer_kernel_ring32_zn_layer19.md (6.263 GB / 4.346 GB).
-TRAFFIC_PER_ALG_BYTE = 1.44
+# profiles/layer_kernel_ring32_zn_layer19.md (7.390 GB / 4.346 GB).
+TRAFFIC_PER_ALG_BYTE = 1.70
 
 
 def peaks():

@@ -591,17 +591,27 @@ __device__ __forceinline__ double ld_coef(const double* c, uint64_t i) { return 
 
 // Find key k among the entries that existed when the gate started (dense
 // position < T0); slots of this gate's births are skipped without reading
-// their keys, so births need no fence before they are published.
+// their keys, so births need no fence before they are published.  With
+// load_coef, a candidate's coefficient is loaded together with its key and
+// stored to *c on a match: one dependent round trip fewer for a caller that
+// needs the coefficient of the entry it finds.
 template <int W>
 __device__ __forceinline__ int64_t index_find_old(const DevTable& t, const Key<W>& k, uint64_t h,
-                                                  uint32_t tag, uint64_t T0, unsigned& err) {
+                                                  uint32_t tag, uint64_t T0, unsigned& err,
+                                                  bool load_coef = false, double* c = nullptr) {
   uint64_t pos = h & t.imask;
   for (uint64_t probe = 0; probe <= t.imask; ++probe) {
     const uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
     if (s == 0) return -1;
     if ((uint32_t)(s >> 32) == tag) {
       const uint32_t idx = (uint32_t)s;
-      if ((uint64_t)idx < T0 && keys_equal(ld_key_cg<W>(t.keys, idx), k)) return (int64_t)idx;
+      if ((uint64_t)idx < T0) {
+        const double cc = load_coef ? ld_coef(t.coef, idx) : 0.0;
+        if (keys_equal(ld_key_cg<W>(t.keys, idx), k)) {
+          if (load_coef) *c = cc;
+          return (int64_t)idx;
+        }
+      }
     }
     pos = (pos + 1) & t.imask;
   }

@@ -172,26 +172,25 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
         const double cQ = ld_coef(t.coef, i);
         const bool liveQ = !is_dead(cQ);
         // The member of {Q, R} with the pivot bit of P clear owns the pair,
-        // decided from keys only.  A truncated member with the bit set has
-        // nothing to do (its partner either owns the pair or is absent), so it
-        // skips the lookup; a truncated owner still looks up, since a live
-        // partner revives it.
-        int64_t jr = -3;
-        if (liveQ || pw == 0) {
-          const uint64_t h = key_hash(R);
-          jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
-        }
+        // decided from keys only.  Every member looks its partner up without
+        // waiting for its own coefficient (a truncated member with the bit set
+        // then has nothing to do: its partner owns the pair or is absent); the
+        // owner loads the partner's coefficient together with its key.
+        const bool owner = pw == 0;
+        double cRo = 0.0;
+        const uint64_t h = key_hash(R);
+        const int64_t jr = index_find_old<W>(t, R, h, tag_of(h), T0, err, owner, &cRo);
         const bool neg = sigma_of<W>(g, Qk) < 0;  // i P Q = -R
-        const double cR = (jr >= 0 && pw == 0) ? ld_coef(t.coef, jr) : 0.0;
+        const double cR = (jr >= 0 && owner) ? cRo : 0.0;
         // live anticommuting strings, counted from values before the gate: the
         // owner counts a stored pair (its partner may be rewriting the other
         // member meanwhile), anyone else counts only itself
         if (jr >= 0)
-          n_ac += pw == 0 ? (unsigned long long)liveQ + (unsigned long long)!is_dead(cR) : 0ull;
+          n_ac += owner ? (unsigned long long)liveQ + (unsigned long long)!is_dead(cR) : 0ull;
         else
           n_ac += liveQ;
         // owner with its partner stored, or a live string whose partner is new
-        const bool own = jr >= 0 && pw == 0 && (liveQ || !is_dead(cR));
+        const bool own = jr >= 0 && owner && (liveQ || !is_dead(cR));
         const bool birth = jr == -1 && liveQ;
         if (own || birth) {
           // one instruction sequence for both cases (a birth has c_R = 0 and
