@@ -89,3 +89,13 @@ def test_null_context_is_an_argument_error(lib):
     for name in ("pp_canonicalize", "pp_merge", "pp_synchronize"):
         assert getattr(lib, name)(None) == 1
     assert lib.pp_truncate(None, 0.0, -1) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libpp.so every call raises: there is no CPU path to fall back on."""
+    monkeypatch.setattr(pp, "_lib", None)
+    monkeypatch.setattr(pp, "_LIB", str(tmp_path / "libpp.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pp.load()
+    with pytest.raises(RuntimeError):
+        pp.pp_config_default(n_qubits=4)
