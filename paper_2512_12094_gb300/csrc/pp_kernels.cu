@@ -13,9 +13,10 @@
 // thread owns each pair (the member whose "pivot" bit of P is clear), reads
 // both coefficients and writes both results, so the update needs no atomics
 // and is computed exactly as cos*c_Q + (+-sin*c_R) in FP64 without FMA
-// contraction.  A partner that is not in the table is appended (warp ballot
-// + one atomic per warp) and inserted into the index; it is unique to its
-// parent, so the insert never races with another insert of the same key.
+// contraction.  A partner that is not in the table is staged in shared
+// memory, appended at the end of the gate (one atomic per block) and
+// inserted into the index; it is unique to its parent, so the insert never
+// races with another insert of the same key.
 #include <cooperative_groups.h>
 
 #include "pp_device.cuh"
