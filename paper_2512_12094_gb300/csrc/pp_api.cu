@@ -2,11 +2,13 @@
 //
 // A context owns two term tables of equal capacity (the live one and a
 // spare used as the destination of merges and compactions), a device
-// control block, and small constant tables.  Gates run as one kernel each;
-// repeated layers are replayed from captured CUDA graphs.  The host reads the
-// control block once per layer: a gate that finds less than twice its input
-// size free does nothing and raises `stall`; the host then grows the tables
-// and relaunches the layer from that gate (earlier gates skip themselves).
+// control block, and small constant tables.  By default all gates of a layer
+// run in one cooperative launch with a grid barrier between gates; otherwise
+// (and for batched rows) each gate is one kernel and repeated layers are
+// replayed from captured CUDA graphs.  The host reads the control block once
+// per layer: a gate that finds less than twice its input size free does
+// nothing and raises `stall`; the host then grows the tables and relaunches
+// the layer from that gate (earlier gates skip themselves).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -75,9 +77,9 @@ struct Buf {
 };
 
 struct ArgsEntry {
-  std::vector<unsigned char> sig;  // bytes of the gate arguments
+  std::vector<unsigned char> sig;  // the cached bytes (gate arguments or cos/sin columns)
   GateArgs* d_args = nullptr;      // device copy
-  size_t n = 0;
+  size_t n = 0;                    // its size in bytes
   uint64_t last_use = 0;
 };
 
@@ -1007,13 +1009,13 @@ pp_status device_args(pp_ctx* c, const std::vector<GateArgs>& args, const GateAr
                                [](const ArgsEntry& a, const ArgsEntry& b) {
                                  return a.last_use < b.last_use;
                                });
-    dfree(c, it->d_args, it->n * sizeof(GateArgs));
+    dfree(c, it->d_args, it->n);
     c->arg_cache.erase(it);
   }
   ArgsEntry ent;
-  ent.n = args.size();
-  PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n * sizeof(GateArgs)));
-  PP_CUDA(upload(c, ent.d_args, args.data(), ent.n * sizeof(GateArgs)));
+  ent.n = args.size() * sizeof(GateArgs);
+  PP_TRY(dmalloc(c, (void**)&ent.d_args, ent.n));
+  PP_CUDA(upload(c, ent.d_args, args.data(), ent.n));
   ent.sig = std::move(sig);
   ent.last_use = c->graph_clock;
   *out = ent.d_args;
@@ -1095,7 +1097,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
                               desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
     c->launches += 1;
   }
-  // room for twice the growth the previous layer showed (at least doubling)
+  // room for 2.5 times the growth the previous layer showed (at least doubling)
   const uint64_t factor =
       std::max<uint64_t>(2, (uint64_t)std::ceil(2.0 * 1.25 * std::max(1.0, c->last_growth)));
   PP_TRY(make_room(c, factor));
@@ -1229,7 +1231,7 @@ pp_status pp_destroy(pp_ctx* c) {
   c->graphs.clear();
   for (auto e : c->ev_start) cudaEventDestroy(e);
   for (auto e : c->ev_end) cudaEventDestroy(e);
-  for (auto& a : c->arg_cache) dfree(c, a.d_args, a.n * sizeof(GateArgs));
+  for (auto& a : c->arg_cache) dfree(c, a.d_args, a.n);
   c->arg_cache.clear();
   for (auto e : c->ev_layer)
     if (e) cudaEventDestroy(e);
