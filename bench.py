@@ -41,6 +41,7 @@ COEF_BYTES = 8   # FP64
 # ncu capture of one full layer of this workload summarised in
 # profiles/layer_kernel_ring32_zn_layer19.md (7.390 GB / 4.346 GB).
 TRAFFIC_PER_ALG_BYTE = 1.70
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, for context beside the measured peak
 
 
 def peaks():
@@ -252,6 +253,8 @@ def bench_ours(args):
                                       "(profiles/layer_kernel_ring32_zn_layer19.md) x this "
                                       "average launch",
                      "kernel": "layer_kernel<1>", "peak_kind": peak_kind,
+                     "peak_nominal": HBM_NOMINAL_GBS,
+                     "frac_nominal": (achieved / HBM_NOMINAL_GBS) if achieved else None,
                      "bytes_model": "16 B key per live term + 64 B per live anticommuting term",
                      "avg_launch_us": 1e3 * gate_ms / max(gate_n, 1),
                      "algorithmic_bytes_per_launch": bytes_alg / max(gate_n, 1),
