@@ -29,12 +29,13 @@ STATUS = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_OOM", 3: "PP_ERR_CAPACITY",
           4: "PP_ERR_SYMMETRY", 5: "PP_ERR_CUDA", 6: "PP_ERR_TIMEOUT", 7: "PP_ERR_BUSY",
           8: "PP_ERR_REJECTED", 9: "PP_ERR_STATE", 10: "PP_ERR_INTERNAL"}
 SYM_NONE, SYM_ZN, SYM_SN, SYM_DN, SYM_TORUS = 0, 1, 2, 3, 4
+NOISE_NONE, NOISE_PER_GATE, NOISE_PER_LAYER = 0, 1, 2
 
 
 def sym_torus(lx: int) -> int:
     """Group code of the translations of an lx x (n / lx) torus (PP_SYM_TORUS_LX)."""
     return SYM_TORUS | (int(lx) << 8)
-NOISE_NONE, NOISE_PER_GATE, NOISE_PER_LAYER = 0, 1, 2
+
 
 _lib = None
 _lock = threading.Lock()
