@@ -117,3 +117,25 @@ def test_batched_column_equals_unbatched_run():
             assert bd[k][b] == v
         assert math.isclose(float(single.expect(wl.state.bloch)),
                             float(prop.expect(wl.state.bloch)[b]), abs_tol=1e-13)
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_batched_at_the_maximum_batch(f32):
+    """B = 512, the largest batch the ABI accepts: FP64 rows bit for bit, FP32
+    rows within the FP32 tolerance (truncation off, so that no term sits on the
+    threshold), overlaps of all 512 columns."""
+    n, B = 8, 512
+    prop, st = run_batched(n, B, 2, 0.0 if f32 else 1e-5, -1, 1, f32, seed=9)
+    g = rows_dict(*prop.export())
+    o = rows_dict(*st.export())
+    assert set(g) == set(o) and len(o) > 10
+    for k in o:
+        if f32:
+            assert float(np.max(np.abs(g[k] - o[k]))) < 1e-5
+        else:
+            np.testing.assert_allclose(g[k], o[k], atol=1e-12, rtol=0)
+    bloch = pi.neel_state(n).bloch
+    got, want = prop.expect(bloch), st.expect(bloch)
+    assert got.shape == (B,)
+    tol = 1e-5 * np.abs(want) + 1e-6 if f32 else 1e-10
+    assert np.all(np.abs(got - want) <= tol)
