@@ -6,6 +6,7 @@ closed form, a count given by Burnside's lemma, the paper's printed example,
 or brute force over group elements.  No GPU is used.
 """
 import itertools
+import json
 import math
 import os
 
@@ -426,3 +427,41 @@ def test_batched_truncation_keeps_a_term_if_any_column_is_large(oracle_lib):
     bx, bz, bc = bst.export()
     got = dict(zip(pi.from_masks(bx, bz, n), map(tuple, bc)))
     assert got == {"ZII": (1e-4, 2e-2), "IYI": (0.5, 0.5)}
+
+
+# ------------------------------------------ the stored expected values
+
+def _trajectory(oracle_lib, wl, group, layers):
+    ox, oz, oc = wl.observable.arrays()
+    st = oracle_lib.OracleState(wl.circuit.n, ox, oz, oc, group=group, eps=wl.eps,
+                                max_weight=wl.max_weight)
+    rows = []
+    for layer in list(reversed(range(len(wl.circuit.layers))))[:layers]:
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        st.apply_layer(gx, gz, th, wl.noise_mode, wl.noise_p, group=group)
+        rows.append({"terms": len(st), "expect": st.expect(wl.state.bloch, group),
+                     "updates": st.updates})
+    return rows
+
+
+def test_stored_heisenberg_trajectory_is_the_oracles_and_the_state_vectors(oracle_lib):
+    """tests/golden/heisenberg_a2a_n8.json was written by write_golden.py from
+    the oracle: the oracle still gives it exactly, and it is the state-vector
+    result (n = 8, 3 Trotter steps, no truncation)."""
+    gold = json.load(open(os.path.join(GOLDEN, "heisenberg_a2a_n8.json")))["plain"]
+    wl = pi.config0_heisenberg()
+    assert _trajectory(oracle_lib, wl, 0, len(gold)) == gold
+    ref = sv.statevector_expectations(wl.circuit.layers, wl.observable.terms, wl.state.bloch)
+    np.testing.assert_allclose([r["expect"] for r in gold], ref, atol=1e-12, rtol=0)
+
+
+def test_stored_ring_trajectories_start_as_the_oracles(oracle_lib):
+    """The first steps of tests/golden/ring_n32.json (plain and Z_32) are what
+    the oracle computes now; the first two steps agree between plain and merged
+    (no term is near eps yet), as Theorem 1 says without truncation."""
+    data = json.load(open(os.path.join(GOLDEN, "ring_n32.json")))
+    wl = pi.config1_ring()
+    assert _trajectory(oracle_lib, wl, 0, 3) == data["plain"][:3]
+    assert _trajectory(oracle_lib, wl, 1, 3) == data["zn"][:3]
+    for k in range(2):
+        assert data["zn"][k]["expect"] == pytest.approx(data["plain"][k]["expect"], abs=1e-14)
