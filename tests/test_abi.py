@@ -6,6 +6,8 @@ which returns before any CUDA call, is exercised.
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -72,6 +74,45 @@ def test_group_codes_in_the_header_match_the_binding(lib):
     assert pp.sym_torus(4) == 4 + 4 * 256
     # a torus width that does not divide n is rejected before any CUDA call
     assert lib.pp_canonical_keys(8, pp.sym_torus(3), 1, None, None, None) == 1
+
+
+def test_status_codes_and_struct_sizes_match_the_header(lib):
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "pp.h")).read(), flags=re.S)
+    body = re.search(r"typedef enum \{(.*?)\} pp_status;", txt, flags=re.S).group(1)
+    declared = {int(v): k for k, v in re.findall(r"(PP_\w+)\s*=\s*(\d+)", body)}
+    assert declared == pp.STATUS
+
+
+def test_binding_structs_have_the_header_layout(tmp_path):
+    """Every ctypes mirror has the size and field offsets that a C compiler
+    gives the structs of include/pp.h."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [pp.pp_config, pp.pp_pauli, pp.pp_stats_t, pp.pp_job, pp.pp_job_result]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pp.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for field in st._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (name, field[0], name, field[0]))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        name, field, value = ln.split()
+        got[(name, field)] = int(value)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(st), name
+        for field in st._fields_:
+            assert got[(name, field[0])] == getattr(st, field[0]).offset, (name, field[0])
 
 
 def test_stateless_calls_validate_arguments(lib):
