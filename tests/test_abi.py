@@ -140,3 +140,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         pp.load()
     with pytest.raises(RuntimeError):
         pp.pp_config_default(n_qubits=4)
+
+
+def test_binding_argument_counts_match_the_prototypes():
+    """Every prototype of include/pp.h and the binding's argtypes agree in arity."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "pp.h")).read(), flags=re.S)
+    protos = re.findall(r"\n(?:pp_status|const char\*)\s+(pp_\w+)\s*\(([^;]*?)\)\s*;", txt,
+                        flags=re.S)
+    assert sorted(name for name, _ in protos) == pp.EXPORTED
+    for name, args in protos:
+        a = args.strip()
+        arity = 0 if a in ("", "void") else len(a.split(","))
+        assert arity == len(pp._SIGS[name]), name
