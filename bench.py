@@ -10,9 +10,10 @@ weight <= 10, FP64.  It is propagated twice, plain and Z_32-merged, and
 
 Prints one JSON line (rank 0).  ``value`` is measured with the observable
 already in device memory; ``e2e`` goes through the host-buffer C-ABI calls
-(pp_create from host arrays, pp_expect back to the host).  ``roofline`` is for
-the gate kernel, timed with CUDA events captured around every gate kernel on
-the context's stream during the timed steps.  ``cpu_baseline`` times the CPU
+(pp_create from host arrays, pp_expect back to the host).  Both timed regions
+run the job without instrumentation.  ``roofline`` is for the layer kernel,
+timed with CUDA events around every layer kernel on the context's stream in a
+separate pass of the same jobs.  ``cpu_baseline`` times the CPU
 oracle on a bounded prefix of the same workload.  With N > 1 (torchrun) every
 rank runs an independent replica of the job (the path does not shard).
 """
@@ -37,10 +38,27 @@ METRIC = "pauli_term_gate_updates_per_s"
 UNIT = "updates/s"
 KEY_BYTES = 16   # one uint64 X word + one uint64 Z word (n = 32)
 COEF_BYTES = 8   # FP64
-# DRAM bytes (read + write) per algorithmic byte of layer_kernel<1>, from the
-# ncu capture of one full layer of this workload summarised in
-# profiles/layer_kernel_ring32_zn_layer19.md (7.390 GB / 4.346 GB).
-TRAFFIC_PER_ALG_BYTE = 1.70
+# DRAM bytes (read + write) per algorithmic byte of layer_kernel<1>, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the last layer
+# of the Z_32-merged job, taken with the kernel sources whose digest is
+# recorded beside it.  When the sources differ from that digest the figure no
+# longer describes the kernel and the JSON line reports traffic as null.
+TRAFFIC_CAPTURE = {"ratio": 1.70, "sources_sha16": "unrecorded"}
+KERNEL_SOURCES = ["paper_2512_12094_gb300/csrc/pp_kernels.cu",
+                  "paper_2512_12094_gb300/csrc/pp_device.cuh",
+                  "paper_2512_12094_gb300/csrc/pp_internal.h"]
+
+
+def kernel_sources_sha16():
+    """Digest of the sources that define layer_kernel<1>."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, for context beside the measured peak
 
 
@@ -190,11 +208,9 @@ def bench_ours(args):
         ms_total, upd, launches = 0.0, 0.0, 0
         split = [0.0, 0.0]
         vals = stats = None
-        ac = gate_ms = 0.0
-        gate_n = 0
         for _ in range(args.steps):
-            # the layer kernels are bracketed by CUDA events on the job's stream
-            vals, stats, ev = timed_job(False, True)
+            # no per-kernel events here: the job exactly as a user runs it
+            vals, stats, ev = timed_job(False, False)
             ms_total += ev[0].elapsed_time(ev[2])
             if args.only == "both":
                 split[0] += ev[0].elapsed_time(ev[1])
@@ -202,9 +218,6 @@ def bench_ours(args):
             for st in stats:
                 upd += st["gate_updates"]
                 launches += st["kernel_launches"]
-                ac += st["anticommuting_terms"]
-                gate_ms += st["gate_kernel_ms"]
-                gate_n += st["gate_kernels_timed"]
         barrier()
         # end to end through the host-buffer API (inputs copied in, result read back)
         e2e_ms = 0.0
@@ -213,7 +226,18 @@ def bench_ours(args):
                 _, _, ev = timed_job(True, False)
                 e2e_ms += ev[0].elapsed_time(ev[2])
         clk = clocks.stop()  # both timed regions
-    pupd = upd
+        barrier()
+        # roofline pass: the same jobs with CUDA events around every layer kernel
+        # on the job's stream (separate from the timed regions above)
+        pupd = ac = gate_ms = 0.0
+        gate_n = 0
+        for _ in range(args.steps):
+            _, pstats, _ = timed_job(False, True)
+            for st in pstats:
+                pupd += st["gate_updates"]
+                ac += st["anticommuting_terms"]
+                gate_ms += st["gate_kernel_ms"]
+                gate_n += st["gate_kernels_timed"]
 
     value, e2e_value, ms_max, e2e_max, total_upd = replica_throughput(dist, ms_total, e2e_ms, upd,
                                                                       dev)
@@ -241,30 +265,50 @@ def bench_ours(args):
                    "l2": "flushed (256 MB write) before every timed job",
                    "parallelism": "replicas" if world > 1 else "single"},
         "breakdown_ms_per_step": {"plain": split[0] / args.steps, "zn": split[1] / args.steps,
-                                  "layer_kernels": gate_ms / args.steps},
-        "result": {"expect": vals, "live_terms": [st["live_terms"] for st in stats]},
+                                  "layer_kernels_instrumented_pass": gate_ms / args.steps},
+        "result": result_summary(vals, stats, args.only),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
-                     "traffic": TRAFFIC_PER_ALG_BYTE * bytes_alg / max(gate_n, 1),
-                     "traffic_basis": "ncu DRAM bytes per algorithmic byte of one full layer "
-                                      "(profiles/layer_kernel_ring32_zn_layer19.md) x this "
-                                      "average launch",
+                     "traffic": traffic_per_launch(bytes_alg / max(gate_n, 1)),
+                     "traffic_basis": "ncu DRAM bytes per algorithmic byte of the last layer "
+                                      "of the Z_32 job x this run's average launch; null when "
+                                      "the kernel sources differ from the captured ones",
                      "kernel": "layer_kernel<1>", "peak_kind": peak_kind,
                      "peak_nominal": HBM_NOMINAL_GBS,
                      "frac_nominal": (achieved / HBM_NOMINAL_GBS) if achieved else None,
                      "bytes_model": "16 B key per live term + 64 B per live anticommuting term",
                      "avg_launch_us": 1e3 * gate_ms / max(gate_n, 1),
                      "algorithmic_bytes_per_launch": bytes_alg / max(gate_n, 1),
-                     "timing": "CUDA events around every layer kernel in the timed steps"},
+                     "timing": "CUDA events around every layer kernel, in a pass of the "
+                               "same jobs after the timed regions"},
         "clocks": clk,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def traffic_per_launch(alg_bytes_per_launch):
+    """DRAM bytes per launch scaled from the capture's ratio, or None when the
+    kernel sources changed since that capture."""
+    if TRAFFIC_CAPTURE["sources_sha16"] != kernel_sources_sha16():
+        return None
+    return TRAFFIC_CAPTURE["ratio"] * alg_bytes_per_launch
+
+
+def result_summary(vals, stats, only):
+    """<O> and live terms of each run; with both runs, the expectation
+    difference between the plain and the Z_32-merged propagation."""
+    out = {"expect": vals, "live_terms": [st["live_terms"] for st in stats]}
+    if only == "both" and len(vals) == 2:
+        out["plain_minus_merged"] = vals[0] - vals[1]
+        out["abs_error_merged_vs_plain"] = abs(vals[0] - vals[1])
+        out["live_terms_merged_over_plain"] = stats[1]["live_terms"] / max(stats[0]["live_terms"], 1)
+    return out
 
 
 def cpu_baseline(seconds=20.0):

@@ -34,7 +34,7 @@ def ring_theta(n, angles):
     return th
 
 
-def run_batched(n, B, steps, eps, wmax, group, f32, seed=0, state=None):
+def run_batched(n, B, steps, eps, wmax, group, f32, seed=0, state=None, noise_p=0.0):
     angles = pi.batched_ring_angles(B, seed)
     layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
     gx, gz, _ = pi.Circuit(n, [layer]).gate_arrays(0)
@@ -42,11 +42,13 @@ def run_batched(n, B, steps, eps, wmax, group, f32, seed=0, state=None):
     obs = pi.mean_z(n)
     x, z, c = obs.arrays()
     coef = np.repeat(c[:, None], B, axis=1)
-    prop = pp.Propagator(n, x, z, coef, symmetry=group, eps=eps, max_weight=wmax, batch=B, f32=f32)
+    mode = pp.NOISE_PER_GATE if noise_p > 0 else pp.NOISE_NONE
+    prop = pp.Propagator(n, x, z, coef, symmetry=group, eps=eps, max_weight=wmax, batch=B, f32=f32,
+                         noise_mode=mode, noise_p=noise_p)
     st = oracle.BatchedOracleState(n, B, x, z, coef, group=group, eps=eps, max_weight=wmax)
     for _ in range(steps):
         prop.apply_layer(gx, gz, th, boundary=True)
-        st.apply_layer(gx, gz, th, group=group)
+        st.apply_layer(gx, gz, th, noise_mode=mode, p=noise_p, group=group)
     return prop, st
 
 
@@ -139,3 +141,41 @@ def test_batched_at_the_maximum_batch(f32):
     assert got.shape == (B,)
     tol = 1e-5 * np.abs(want) + 1e-6 if f32 else 1e-10
     assert np.all(np.abs(got - want) <= tol)
+
+
+@pytest.mark.parametrize("n,B,eps,wmax,group", [(10, 8, 1e-4, 6, 0), (12, 16, 1e-4, 5, 1),
+                                                 (64, 8, 1e-3, 4, 0)])
+def test_batched_fp64_per_gate_noise_bitexact(n, B, eps, wmax, group):
+    """Per-gate depolarising damping (1-p)^k on batched FP64 rows: the same
+    per-column operations as the batched oracle, so without a merge the term
+    sets and coefficients are bit-identical; with a Z_n merge (FP64 atomics)
+    within 1e-12."""
+    prop, st = run_batched(n, B, 3, eps, wmax, group, False, seed=4, noise_p=0.02)
+    g = rows_dict(*prop.export())
+    o = rows_dict(*st.export())
+    assert set(g) == set(o) and len(o) > 10
+    for k in o:
+        if group == 0:
+            np.testing.assert_array_equal(g[k], o[k])
+        else:
+            np.testing.assert_allclose(g[k], o[k], atol=1e-12, rtol=0)
+    bloch = pi.neel_state(n).bloch
+    np.testing.assert_allclose(prop.expect(bloch), st.expect(bloch), atol=1e-10, rtol=0)
+
+
+@pytest.mark.parametrize("group", [0, 1])
+def test_batched_fp32_per_gate_noise_within_fp32_tolerance(group):
+    """FP32 rows with per-gate damping: the damping factors and the rotation are
+    applied in FP32, merges and overlaps in FP64.  Truncation is off so that no
+    term sits on the threshold; <O> per column agrees with the FP64 oracle
+    within 1e-5 relative (plus a 1e-6 floor)."""
+    n, B = 10, 24
+    prop, st = run_batched(n, B, 3, 0.0, 6, group, True, seed=6, noise_p=0.05)
+    g = rows_dict(*prop.export())
+    o = rows_dict(*st.export())
+    assert set(g) == set(o)
+    worst = max(float(np.max(np.abs(g[k] - o[k]))) for k in o)
+    assert worst < 1e-5
+    bloch = pi.neel_state(n).bloch
+    got, want = prop.expect(bloch), st.expect(bloch)
+    assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-6)

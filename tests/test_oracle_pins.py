@@ -419,6 +419,68 @@ def test_batched_single_column_equals_single_state_with_truncation(oracle_lib):
     np.testing.assert_array_equal(bc[:, 0], sc)
 
 
+def _column_layers(circ, angles_per_gate, b):
+    """The circuit's layers with gate k of the flattened circuit at angle
+    angles_per_gate[k, b] (time order)."""
+    out, k = [], 0
+    for layer in circ.layers:
+        row = []
+        for s, _ in layer:
+            row.append((s, float(angles_per_gate[k, b])))
+            k += 1
+        out.append(row)
+    return out
+
+
+@pytest.mark.parametrize("p", [0.07, 0.3])
+def test_batched_per_gate_noise_matches_density_matrix_per_column(oracle_lib, p):
+    """Batched rows with per-gate depolarising damping: every column is its own
+    noisy circuit (own angles, same gates), so column b must equal the density
+    matrix evolved with column b's angles and the channel after every gate on
+    its support.  Damping applied after the rotation instead of before it, or
+    with the support count of the wrong string, changes these values."""
+    n, B = 4, 3
+    circ = pi.random_circuit(n, n_layers=2, gates_per_layer=6, seed=31, max_support=2)
+    n_gates = sum(len(l) for l in circ.layers)
+    angles = np.random.default_rng(32).uniform(-math.pi, math.pi, size=(n_gates, B))
+    obs = pi.random_observable(n, 4, seed=33, max_weight=2)
+    state = pi.random_product_state(n, 34)
+    x, z, c = obs.arrays()
+    bst = oracle_lib.BatchedOracleState(n, B, x, z, np.repeat(c[:, None], B, axis=1))
+    k_end = n_gates
+    for li in reversed(range(len(circ.layers))):
+        K = len(circ.layers[li])
+        gx, gz = pi.to_masks([s for s, _ in circ.layers[li]], n)
+        bst.apply_layer(gx, gz, angles[k_end - K:k_end], noise_mode=1, p=p)
+        k_end -= K
+    got = bst.expect(state.bloch)
+    for b in range(B):
+        ref = sv.density_expectations(n, _column_layers(circ, angles, b), obs.terms, state.bloch,
+                                      p_gate=p)[-1]
+        assert got[b] == pytest.approx(ref, abs=1e-12)
+    assert len(set(np.round(got, 9))) == B  # the columns really differ
+
+
+def test_batched_noise_single_column_equals_single_state(oracle_lib):
+    """One column with per-gate damping and truncation is the single-column
+    oracle, coefficient for coefficient."""
+    n = 6
+    wl = pi.config1_ring(n=n, steps=3, eps=1e-3, max_weight=4)
+    x, z, c = wl.observable.arrays()
+    bst = oracle_lib.BatchedOracleState(n, 1, x, z, c[:, None], eps=wl.eps,
+                                        max_weight=wl.max_weight)
+    st = oracle_lib.OracleState(n, x, z, c, eps=wl.eps, max_weight=wl.max_weight)
+    for layer in range(3):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        bst.apply_layer(gx, gz, th[:, None], noise_mode=1, p=0.05)
+        st.apply_layer(gx, gz, th, noise_mode=1, p=0.05)
+    bx, bz, bc = bst.export()
+    sx, sz, sc = st.export()
+    np.testing.assert_array_equal(bx, sx)
+    np.testing.assert_array_equal(bz, sz)
+    np.testing.assert_array_equal(bc[:, 0], sc)
+
+
 def test_batched_truncation_keeps_a_term_if_any_column_is_large(oracle_lib):
     n = 3
     x, z = pi.to_masks(["ZII", "XII", "IYI"], n)
