@@ -605,6 +605,126 @@ def bench_workload(args):
                               "config": {"workload": "canonical_keys_n64_%s_16M" % label},
                               "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
                                       "peak_kind": kind}}), flush=True)
+    if "merge32" in names:
+        # the Z_32 boundary merge of the ring job: the table after the gates of
+        # the last layer (before its merge), merged by hash and by sort
+        wl = pi.config1_ring(symmetry=1)
+        layers = packed_layers(wl)
+        prop = pp.Propagator.from_workload(wl, symmetry=1)
+        for packed, th in layers[:-1]:
+            pp.pp_apply_layer(prop.ctx, packed, th, True)
+        pp.pp_apply_layer(prop.ctx, layers[-1][0], layers[-1][1], False)
+        x, z, c = prop.export()
+        prop.close()
+        m = len(c)
+        keys = torch.from_numpy(np.ascontiguousarray(np.concatenate([x, z], axis=1)).view(np.int64)).cuda()
+        coef = torch.from_numpy(c).cuda()
+        out_k, out_c = torch.empty_like(keys), torch.empty_like(coef)
+        res = {}
+        for label, fn in (("hash", pp.pp_merge_terms), ("sort", pp.pp_merge_terms_sorted)):
+            for _ in range(2):
+                res[label + "_distinct"] = fn(32, 1, m, keys, coef, out_k, out_c)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(5):
+                fn(32, 1, m, keys, coef, out_k, out_c)
+            t1.record()
+            torch.cuda.synchronize()
+            res[label + "_ms"] = t0.elapsed_time(t1) / 5
+        print(json.dumps({"metric": "boundary_merge_ms", "unit": "ms", "n_gpus": 1,
+                          "data": "synthetic", "higher_is_better": False,
+                          "config": {"workload": "ring_n32_Z32_last_boundary_merge",
+                                     "input_terms": m},
+                          "result": res}), flush=True)
+        # the whole Z_32 job with each merge method
+        for method, label in ((pp.MERGE_HASH, "hash"), (pp.MERGE_SORT, "sort")):
+            make = lambda: pp.Propagator.from_workload(wl, symmetry=1, merge_method=method)  # noqa: E731
+            _timed_run(pp, make, layers)
+            ms = [_timed_run(pp, make, layers, bloch=wl.state.bloch) for _ in range(3)]
+            line("ring_n32_Z32_job_merge_" + label, min(r[0] for r in ms), ms[0][1]["gate_updates"],
+                 {"result": {"expect": ms[0][3], "live_terms": ms[0][2]},
+                  "ms_all": [r[0] for r in ms]})
+    if "rows64" in names:
+        # batched rows (ring n=64, B = 256, 3 steps) merged by hash and by sort
+        n, B, steps = 64, 256, 3
+        angles = pi.batched_ring_angles(B, 0)
+        layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
+        gx, gz, _ = pi.Circuit(n, [layer]).gate_arrays(0)
+        th = np.zeros((3 * n, B))
+        th[:n], th[n:2 * n], th[2 * n:] = angles[:, 0], angles[:, 1], angles[:, 2]
+        x, z, c = pi.mean_z(n).arrays()
+        coef = np.repeat(c[:, None], B, axis=1)
+        packed = pp.pack_gates(gx, gz)
+        for f32 in (False, True):
+            for method, label in ((pp.MERGE_HASH, "hash"), (pp.MERGE_SORT, "sort")):
+                make = lambda: pp.Propagator(n, x, z, coef, symmetry=1, eps=1e-5, batch=B,  # noqa: E731
+                                             f32=f32, merge_method=method)
+                _timed_run(pp, make, [(packed, th)])
+                ms, st, live, _ = _timed_run(pp, make, [(packed, th)] * steps)
+                line("ring64_B256_%s_Z64_3steps_merge_%s" % ("fp32" if f32 else "fp64", label), ms,
+                     st["gate_updates"] * B, {"unit_note": "column updates",
+                                              "result": {"live_terms": live}})
+    if "cadence" in names:
+        # merge cadence: a symmetry merge after every k-th layer (or sublayer);
+        # GPU time and table sizes, and <O> next to the oracle on the same schedule
+        def sweep(wl, group, schedules, with_oracle, label):
+            for every, sub in schedules:
+                run = pi.split_sublayers(wl) if sub else wl
+                L = len(run.circuit.layers)
+                flags = pi.merge_schedule(L, every)
+                layers_r = packed_layers(run)
+
+                def job(record=False):
+                    prop = pp.Propagator.from_workload(run, symmetry=group)
+                    peak = 0
+                    for (packed, th), f in zip(layers_r, flags):
+                        pp.pp_apply_layer(prop.ctx, packed, th, f)
+                        if record:
+                            peak = max(peak, prop.num_terms()[0])
+                    return prop, peak
+
+                prop, peak = job(record=True)
+                val = prop.expect(run.state.bloch)
+                live = prop.num_terms()[0]
+                prop.close()
+                times = []
+                for _ in range(3):
+                    torch.cuda.synchronize()
+                    t0 = torch.cuda.Event(enable_timing=True)
+                    t1 = torch.cuda.Event(enable_timing=True)
+                    t0.record()
+                    prop, _ = job()
+                    prop.expect(run.state.bloch)
+                    t1.record()
+                    torch.cuda.synchronize()
+                    st = prop.stats()
+                    prop.close()
+                    times.append(t0.elapsed_time(t1))
+                res = {"expect": val, "live_terms": live, "peak_live_terms": peak,
+                       "merges": int(sum(flags))}
+                if with_oracle:
+                    import oracle
+                    t = time.perf_counter()
+                    ox, oz, oc = run.observable.arrays()
+                    ost = oracle.OracleState(run.circuit.n, ox, oz, oc, group=group, eps=run.eps,
+                                             max_weight=run.max_weight)
+                    for layer, f in zip(reversed(range(L)), flags):
+                        gx, gz, th = run.circuit.gate_arrays(layer)
+                        ost.apply_layer(gx, gz, th, run.noise_mode, run.noise_p,
+                                        group=group if f else 0)
+                    ov = ost.expect(run.state.bloch, group)
+                    res.update({"oracle_expect": ov, "abs_error_vs_oracle": abs(val - ov),
+                                "oracle_s": time.perf_counter() - t})
+                line("%s_merge_every_%d%s" % (label, every, "_sublayers" if sub else "_layers"),
+                     min(times), st["gate_updates"], {"result": res, "ms_all": times})
+
+        sched = [(1, False), (2, False), (4, False), (1, True), (2, True)]
+        sweep(pi.config1_ring(n=32, symmetry=1), 1, sched, False, "ring32_Z32")
+        sweep(pi.config1_ring(n=16, steps=10, eps=1e-4, max_weight=8, symmetry=1), 1, sched, True,
+              "ring16_Z16")
+        sweep(pi.xxz_all_to_all(20, 0.05, 4, eps=0.01, symmetry=2, split=True), 2,
+              [(1, False), (3, False)], True, "xxz20_S20_12_sublayers")
     if "xxz36" in names:
         wl = pi.xxz_all_to_all(36, 0.05, 6, eps=0.05, symmetry=2, split=True)
         layers = packed_layers(wl, 16)
@@ -654,7 +774,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--workload", default="",
-                    help="comma list of a2a64, batched64, columns64, xxz36, canon64: time those")
+                    help="comma list of a2a64, batched64, columns64, xxz36, canon64, merge32, "
+                         "rows64, cadence: time those")
     ap.add_argument("--profile-layer", type=int, default=-1,
                     help="run the Z_n job once, bracketing layer K for ncu --profile-from-start off")
     args = ap.parse_args()

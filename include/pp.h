@@ -74,6 +74,18 @@ typedef enum {
 typedef enum { PP_COEF_F64 = 0, PP_COEF_F32 = 1 } pp_coef_type;
 typedef enum { PP_NOISE_NONE = 0, PP_NOISE_PER_GATE = 1, PP_NOISE_PER_LAYER = 2 } pp_noise_mode;
 
+/* How identical strings (or representatives) are accumulated by a merge --
+ * the "if s~ is in D~ accumulate, else insert" loop of Algorithms 2 and 3:
+ *  PP_MERGE_HASH  open-addressing device hash table, atomicCAS on key slots and
+ *                 FP64 atomicAdd on coefficients (rounding order not fixed);
+ *  PP_MERGE_SORT  LSD radix sort of the representatives and a segmented FP64
+ *                 reduce of each run of equal keys in input order: the sums are
+ *                 reproducible bit for bit.  Needs n_qubits <= 64; wider
+ *                 strings, or a scratch that would not fit the memory budget,
+ *                 use the hash table.  Its scratch (about 41 bytes per table
+ *                 entry for n <= 32, 57 for n <= 64) stays with the context. */
+typedef enum { PP_MERGE_HASH = 0, PP_MERGE_SORT = 1 } pp_merge_method;
+
 /* A Pauli rotation generator P: words [0, W) of x and z are used, the rest
  * must be zero. */
 typedef struct {
@@ -104,6 +116,13 @@ typedef struct {
   int layer_kernel;        /* nonzero (default): all gates of a layer run in one persistent
                               cooperative kernel with a grid barrier between gates; zero:
                               one kernel per gate, replayed from CUDA graphs */
+  int merge_method;        /* pp_merge_method of the symmetry and identical-string merges
+                              after ingest (ingest itself uses the hash table) */
+  int wait_limit;          /* polls a bounded device wait (the grid barrier between gates,
+                              a merge waiting for a claimed index slot) may take before it
+                              gives up: the kernel records the failure and returns, and the
+                              call reports PP_ERR_TIMEOUT; 0 = the default, 2^22 polls
+                              (about a second).  >= 0. */
 } pp_config;
 
 typedef struct pp_ctx pp_ctx;
@@ -124,6 +143,10 @@ typedef struct {
                               gates (one per layer, or one per gate without layer_kernel) */
   int64_t gate_kernels_timed; /* number of launches summed in gate_kernel_ms */
   double grid_scale;       /* blocks per gate pass relative to the default sizing (pp_tune) */
+  double skipped_updates;  /* the part of gate_updates from gates that no stored string could
+                              anticommute with (nor, with per-gate noise, overlap): the layer
+                              kernel tests them against the OR of all keys and skips the scan */
+  int64_t gates_skipped;   /* number of such gates */
 } pp_stats_t;
 
 /* Fill *cfg with defaults: n_qubits = 0 (must be set), no symmetry, batch 1,
@@ -252,6 +275,14 @@ pp_status pp_synchronize(pp_ctx* ctx);
 /* Message describing the calling thread's most recent failure ("" if none). */
 const char* pp_last_error(void);
 
+/* Host-side fault injection for tests of failure handling (the paper has no
+ * counterpart).  After n further device allocations by any context of this
+ * process, the next one fails as if the device were out of memory: the call
+ * that needed it returns PP_ERR_OOM.  Table growth that fails this way leaves
+ * the context as it was before the call, so it may be used again.  The
+ * injection fires once; n < 0 turns it off.  Never touches the GPU. */
+pp_status pp_debug_fail_alloc_after(int64_t n);
+
 /* ------------------------------------------------------------------------
  * Stateless entry points on caller-owned device arrays.  Keys are device
  * arrays [m][2W] with the x words of a string followed by its z words.  All
@@ -274,6 +305,17 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
                          const double* coef_in, uint64_t* keys_out, double* coef_out,
                          int64_t* m_out, void* stream);
 
+/* pp_merge_terms by radix sort and segmented reduce (PP_MERGE_SORT): the
+ * distinct strings come out in ascending order of the packed key (x | z << 32
+ * for n <= 32, otherwise z then x as a 128-bit integer), and each sum is taken
+ * in input order, so the output is the same bit for bit on every call.
+ * n_qubits must be at most 64 (PP_ERR_ARG otherwise).  Uses temporary device
+ * memory from cudaMallocAsync on `stream` (about 41 or 57 bytes per input
+ * term); synchronises the stream. */
+pp_status pp_merge_terms_sorted(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                                const double* coef_in, uint64_t* keys_out, double* coef_out,
+                                int64_t* m_out, void* stream);
+
 /* *out (device pointer, one double) = sum_i coef[i] ov(keys[i]), ov the
  * product-state overlap of pp_expect (orbit-averaged under `symmetry`),
  * bloch a device array [n][3].  Deterministic two-pass FP64 reduction. */
@@ -292,10 +334,13 @@ typedef struct pp_server pp_server;
  * applied n_layers times (Trotter steps; pp_apply_layer semantics, with the
  * symmetry merge after each layer when symmetric_boundary != 0), and the
  * product state bloch [n][3].  cfg.cuda_stream and cfg.mem_budget_bytes are
- * set by the server.  mem_bytes: device memory reserved for the job while it
- * runs (0 = the server's default); a job that needs more is retried with four
- * times the reservation, up to the server budget.  All arrays are copied by
- * pp_submit. */
+ * set by the server.  mem_bytes: device memory reserved for the job when it
+ * is admitted (0 = the server's default, or an estimate from n_terms when the
+ * server has none).  The reservation then follows the job: before each layer
+ * it is raised to the context's device memory times the growth of its
+ * live-term count over the previous layer, and a layer that still runs out of
+ * room is applied again (from the state before it) with twice the
+ * reservation, up to the server budget.  All arrays are copied by pp_submit. */
 typedef struct {
   pp_config cfg;
   int64_t n_terms;
@@ -323,13 +368,20 @@ typedef struct {
   double run_ms;        /* start -> finish */
   double latency_ms;    /* submit -> finish */
   char message[160];    /* the failing call's error text when status != PP_OK */
+  int grows;            /* times the reservation was raised while the job ran */
+  int restarts;         /* times the job gave its memory back and started again (only
+                           when every running job was waiting for memory) */
 } pp_job_result;
 
 /* A server with `slots` worker threads, each owning a CUDA stream on the
  * calling thread's current device.  Jobs are admitted oldest first among
  * those whose reservation fits in mem_budget_bytes minus the reservations of
- * running jobs; their kernels overlap on the device.  default_job_bytes = 0
- * picks 64 MiB.  Errors: PP_ERR_ARG, PP_ERR_CUDA. */
+ * running jobs; their kernels overlap on the device.  A running job waiting
+ * for a larger reservation is served before any queued job is admitted, and
+ * a queued job that younger ones have passed 8 times is not passed again.
+ * default_job_bytes: reservation of jobs that name none; 0 = estimate each
+ * from its observable (two tables with room for 4 n_terms strings plus fixed
+ * buffers).  Errors: PP_ERR_ARG, PP_ERR_CUDA. */
 pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_job_bytes,
                            pp_server** out);
 

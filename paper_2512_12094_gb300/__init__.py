@@ -19,7 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _LIB = os.path.join(_HERE, "libpp.so")
-_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu", "pp_batched.cu", "pp_server.cu"]
+_SOURCES = ["pp_kernels.cu", "pp_api.cu", "pp_static.cu", "pp_batched.cu", "pp_server.cu",
+            "pp_sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -30,6 +31,7 @@ STATUS = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_OOM", 3: "PP_ERR_CAPACITY",
           8: "PP_ERR_REJECTED", 9: "PP_ERR_STATE", 10: "PP_ERR_INTERNAL"}
 SYM_NONE, SYM_ZN, SYM_SN, SYM_DN, SYM_TORUS = 0, 1, 2, 3, 4
 NOISE_NONE, NOISE_PER_GATE, NOISE_PER_LAYER = 0, 1, 2
+MERGE_HASH, MERGE_SORT = 0, 1
 
 
 def sym_torus(lx: int) -> int:
@@ -92,7 +94,8 @@ class pp_config(ctypes.Structure):
                 ("noise_p", ctypes.c_double), ("mem_budget_bytes", ctypes.c_size_t),
                 ("cuda_stream", ctypes.c_void_p), ("check_symmetry", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("profile_kernels", ctypes.c_int),
-                ("layer_kernel", ctypes.c_int)]
+                ("layer_kernel", ctypes.c_int), ("merge_method", ctypes.c_int),
+                ("wait_limit", ctypes.c_int)]
 
 
 class pp_pauli(ctypes.Structure):
@@ -112,7 +115,8 @@ class pp_job_result(ctypes.Structure):
                 ("live_terms", ctypes.c_int64), ("gate_updates", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("reserved_bytes", ctypes.c_size_t),
                 ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double), ("message", ctypes.c_char * 160)]
+                ("latency_ms", ctypes.c_double), ("message", ctypes.c_char * 160),
+                ("grows", ctypes.c_int), ("restarts", ctypes.c_int)]
 
 
 class pp_stats_t(ctypes.Structure):
@@ -122,7 +126,8 @@ class pp_stats_t(ctypes.Structure):
                 ("compactions", ctypes.c_int64), ("regrows", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("anticommuting_terms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("gate_kernel_ms", ctypes.c_double),
-                ("gate_kernels_timed", ctypes.c_int64), ("grid_scale", ctypes.c_double)]
+                ("gate_kernels_timed", ctypes.c_int64), ("grid_scale", ctypes.c_double),
+                ("skipped_updates", ctypes.c_double), ("gates_skipped", ctypes.c_int64)]
 
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -151,8 +156,11 @@ _SIGS = {
     "pp_set_budget": [_vp, ctypes.c_size_t],
     "pp_synchronize": [_vp],
     "pp_last_error": [],
+    "pp_debug_fail_alloc_after": [ctypes.c_int64],
     "pp_canonical_keys": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp],
     "pp_merge_terms": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _i64p, _vp],
+    "pp_merge_terms_sorted": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _i64p,
+                              _vp],
     "pp_overlap_sum": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp],
     "pp_merge_terms_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                _vp],
@@ -344,6 +352,11 @@ def pp_last_error() -> str:
     return load().pp_last_error().decode()
 
 
+def pp_debug_fail_alloc_after(n: int):
+    """Make the allocation after the next n fail as out of memory (n < 0: off)."""
+    _check(load().pp_debug_fail_alloc_after(int(n)))
+
+
 def pp_canonical_keys(n_qubits: int, symmetry: int, m: int, keys_in, keys_out, stream=None):
     _check(load().pp_canonical_keys(n_qubits, symmetry, int(m), _ptr(keys_in), _ptr(keys_out),
                                     _stream(stream)))
@@ -355,6 +368,15 @@ def pp_merge_terms(n_qubits: int, symmetry: int, m: int, keys_in, coef_in, keys_
     _check(load().pp_merge_terms(n_qubits, symmetry, int(m), _ptr(keys_in), _ptr(coef_in),
                                  _ptr(keys_out), _ptr(coef_out), ctypes.byref(mo),
                                  _stream(stream)))
+    return mo.value
+
+
+def pp_merge_terms_sorted(n_qubits: int, symmetry: int, m: int, keys_in, coef_in, keys_out,
+                          coef_out, stream=None) -> int:
+    mo = ctypes.c_int64()
+    _check(load().pp_merge_terms_sorted(n_qubits, symmetry, int(m), _ptr(keys_in), _ptr(coef_in),
+                                        _ptr(keys_out), _ptr(coef_out), ctypes.byref(mo),
+                                        _stream(stream)))
     return mo.value
 
 
@@ -446,7 +468,8 @@ class Propagator:
 
     def __init__(self, n_qubits, x, z, coef, symmetry=SYM_NONE, eps=0.0, max_weight=-1,
                  noise_mode=NOISE_NONE, noise_p=0.0, budget=0, stream=None, use_graphs=True,
-                 check_symmetry=True, profile=False, layer_kernel=True, batch=1, f32=False):
+                 check_symmetry=True, profile=False, layer_kernel=True, batch=1, f32=False,
+                 merge_method=MERGE_HASH):
         self.n = n_qubits
         self.cfg = pp_config_default(n_qubits=n_qubits, symmetry=symmetry, coeff_eps=eps,
                                      max_weight=max_weight, noise_mode=noise_mode,
@@ -455,7 +478,7 @@ class Propagator:
                                      check_symmetry=int(check_symmetry),
                                      profile_kernels=int(profile),
                                      layer_kernel=int(layer_kernel), batch=int(batch),
-                                     coef_type=1 if f32 else 0)
+                                     coef_type=1 if f32 else 0, merge_method=int(merge_method))
         self.batch = int(batch)
         self.ctx = pp_create(self.cfg, x, z, coef)
         self._packed = {}

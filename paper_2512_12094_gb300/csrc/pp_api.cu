@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -144,6 +145,8 @@ struct pp_ctx {
   double grid_scale = 1.0;   // blocks per launch relative to the default sizing (pp_tune)
   double gate_ms = 0.0;
   int64_t gates_timed = 0;
+  void* sort_scratch = nullptr;  // scratch of the sort-based merge (merge_method 1)
+  size_t sort_scratch_bytes = 0;
 };
 
 namespace {
@@ -204,8 +207,21 @@ void pinned_put(void* p, size_t bytes) {
   cudaFreeHost(p);
 }
 
+// Host-side fault injection (pp_debug_fail_alloc_after): allocations left
+// before one fails as if the device were out of memory; negative = off.
+std::atomic<long long> g_fail_alloc_after{-1};
+
 pp_status dmalloc(pp_ctx* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  for (long long left = g_fail_alloc_after.load(); left >= 0;) {
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {
+        *p = nullptr;
+        return fail(PP_ERR_OOM, "device allocation failed (injected by pp_debug_fail_alloc_after)");
+      }
+      break;
+    }
+  }
   cudaMemPool_t pool = lib_pool();
   cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, c->stream)
                        : cudaMallocAsync(p, bytes, c->stream);
@@ -225,21 +241,6 @@ void dfree(pp_ctx* c, void* p, size_t bytes) {
 // full (a gate stalls before that can happen) and is about 1/4 at a layer start.
 uint64_t index_cap_for(uint64_t cap) { return next_pow2(cap + cap / 2); }
 
-pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
-  b.cap = cap;
-  b.icap = index_cap_for(cap);
-  PP_TRY(dmalloc(c, (void**)&b.keys, (size_t)cap * 16 * c->W));
-  if (c->batched) {
-    PP_TRY(dmalloc(c, (void**)&b.rows, (size_t)cap * c->B * c->esize));
-    PP_TRY(dmalloc(c, (void**)&b.alive, (size_t)cap));
-  } else {
-    PP_TRY(dmalloc(c, (void**)&b.coef, (size_t)cap * 8));
-  }
-  PP_TRY(dmalloc(c, (void**)&b.index, (size_t)b.icap * 8));
-  PP_CUDA(cudaMemsetAsync(b.index, 0, (size_t)b.icap * 8, c->stream));
-  return PP_OK;
-}
-
 void free_buf(pp_ctx* c, Buf& b) {
   dfree(c, b.keys, (size_t)b.cap * 16 * c->W);
   dfree(c, b.coef, (size_t)b.cap * 8);
@@ -247,6 +248,28 @@ void free_buf(pp_ctx* c, Buf& b) {
   dfree(c, b.alive, (size_t)b.cap);
   dfree(c, b.index, (size_t)b.icap * 8);
   b = Buf();
+}
+
+// All arrays of a table of `cap` entries, or none: a failed allocation
+// releases what was taken and leaves b empty.
+pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
+  b = Buf();
+  b.cap = cap;
+  b.icap = index_cap_for(cap);
+  pp_status st = dmalloc(c, (void**)&b.keys, (size_t)cap * 16 * c->W);
+  if (st == PP_OK && c->batched) {
+    st = dmalloc(c, (void**)&b.rows, (size_t)cap * c->B * c->esize);
+    if (st == PP_OK) st = dmalloc(c, (void**)&b.alive, (size_t)cap);
+  } else if (st == PP_OK) {
+    st = dmalloc(c, (void**)&b.coef, (size_t)cap * 8);
+  }
+  if (st == PP_OK) st = dmalloc(c, (void**)&b.index, (size_t)b.icap * 8);
+  if (st == PP_OK) {
+    const cudaError_t e = cudaMemsetAsync(b.index, 0, (size_t)b.icap * 8, c->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (st != PP_OK) free_buf(c, b);
+  return st;
 }
 
 DevTable desc_of(const pp_ctx* c, const Buf& b) {
@@ -299,7 +322,9 @@ pp_status read_ctl(pp_ctx* c) {
 pp_status check_device_error(pp_ctx* c) {
   unsigned e = c->h_ctl->error;
   if (!e) return PP_OK;
-  if (e & kErrTimeout) return fail(PP_ERR_TIMEOUT, "device wait for a published index slot ran out");
+  if (e & kErrTimeout)
+    return fail(PP_ERR_TIMEOUT,
+                "a bounded device wait (grid barrier or claimed index slot) ran out");
   if (e & kErrAppend) return fail(PP_ERR_INTERNAL, "append past table capacity");
   return fail(PP_ERR_INTERNAL, "hash index probe bound exhausted");
 }
@@ -314,8 +339,10 @@ int grid_for(pp_ctx* c, uint64_t items, int per_thread) {
 
 // Set n_next (append cursor) and n_live before a merge or compaction into
 // the spare table (a one-thread kernel on the stream: no host round trip).
-pp_status ctl_prepare_insert(pp_ctx* c, unsigned long long first_free) {
-  PP_CUDA(launch_ctl_insert(c->stream, c->d_ctl, first_free));
+// reset_occ: the table being filled becomes the active one, so its keys
+// rebuild the occupancy masks.
+pp_status ctl_prepare_insert(pp_ctx* c, unsigned long long first_free, bool reset_occ = true) {
+  PP_CUDA(launch_ctl_insert(c->stream, c->d_ctl, first_free, 0, reset_occ ? 1 : 0));
   c->launches += 1;
   return PP_OK;
 }
@@ -362,14 +389,34 @@ pp_status ensure_capacity(pp_ctx* c, uint64_t need) {
   if (c->cfg.mem_budget_bytes && keep + add > c->cfg.mem_budget_bytes)
     return fail(PP_ERR_CAPACITY, "term table of capacity " + std::to_string(cap) +
                                      " exceeds the memory budget");
+  // A failed allocation leaves the context as it was: the spare table is put
+  // back at the capacity it had (the pool has just received those bytes), or
+  // the active table keeps its entries at the larger capacity.
+  const uint64_t old_cap = c->buf[c->active].cap;
   int spare = 1 - c->active;
   free_buf(c, c->buf[spare]);
-  PP_TRY(alloc_buf(c, c->buf[spare], cap));
+  pp_status st = alloc_buf(c, c->buf[spare], cap);
+  if (st != PP_OK) {
+    const std::string msg = g_last_error;
+    if (alloc_buf(c, c->buf[spare], old_cap) == PP_OK) PP_TRY(publish_desc(c));
+    return fail(st, msg);
+  }
   PP_TRY(publish_desc(c));
   PP_TRY(compact_into(c, spare, 0.0, -1));
   int old = 1 - c->active;
   free_buf(c, c->buf[old]);
-  PP_TRY(alloc_buf(c, c->buf[old], cap));
+  st = alloc_buf(c, c->buf[old], cap);
+  if (st != PP_OK) {
+    // the entries now live in the larger table; restore a spare of the old size
+    // would break the equal-capacity rule, so move them back
+    const std::string msg = g_last_error;
+    if (alloc_buf(c, c->buf[old], old_cap) == PP_OK && publish_desc(c) == PP_OK &&
+        compact_into(c, old, 0.0, -1) == PP_OK) {
+      free_buf(c, c->buf[1 - c->active]);
+      if (alloc_buf(c, c->buf[1 - c->active], old_cap) == PP_OK) PP_TRY(publish_desc(c));
+    }
+    return fail(st, msg);
+  }
   PP_TRY(publish_desc(c));
   c->regrows++;
   return PP_OK;
@@ -395,6 +442,27 @@ pp_status make_room(pp_ctx* c, uint64_t factor = 2) {
   return ensure_capacity(c, least);
 }
 
+// Scratch for a sort-based merge of up to `count` entries, kept by the
+// context between merges.  False (use the hash merge) when merges are to use
+// the hash table, the strings are too wide for the sort, or the scratch would
+// not fit in the memory budget.
+bool sort_merge_ready(pp_ctx* c, uint64_t count) {
+  if (c->cfg.merge_method != PP_MERGE_SORT || !sort_merge_supported(c->n)) return false;
+  const size_t need = sort_merge_scratch_bytes(std::max<uint64_t>(count, 1), c->n);
+  if (need <= c->sort_scratch_bytes) return true;
+  const size_t grow = need - c->sort_scratch_bytes;
+  if (c->cfg.mem_budget_bytes && c->bytes + grow > c->cfg.mem_budget_bytes) return false;
+  dfree(c, c->sort_scratch, c->sort_scratch_bytes);
+  c->sort_scratch = nullptr;
+  c->sort_scratch_bytes = 0;
+  if (dmalloc(c, &c->sort_scratch, need) != PP_OK) {
+    c->sort_scratch = nullptr;
+    return false;
+  }
+  c->sort_scratch_bytes = need;
+  return true;
+}
+
 // Accumulate the active table (after optional canonicalisation) into the
 // spare table and make it active: the merge of Algorithms 2 and 3.
 pp_status merge_active(pp_ctx* c, int group) {
@@ -403,7 +471,17 @@ pp_status merge_active(pp_ctx* c, int group) {
   Buf& s = c->buf[c->active];
   PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
   PP_TRY(ctl_prepare_insert(c, 0));
-  if (c->batched) {
+  if (sort_merge_ready(c, c->n_terms)) {
+    // radix sort + segmented reduce; batched rows are finalized by the reduce
+    PP_CUDA(launch_merge_sorted(group, c->n, -1, c->stream, s.keys, c->batched ? nullptr : s.coef,
+                                s.rows, c->f32, s.alive, c->n_terms, nullptr,
+                                c->cfg.coeff_eps > 0.0 ? 1 : 0, desc_of(c, d), 1,
+                                c->cfg.coeff_eps, c->d_ctl, c->sort_scratch, 0));
+    if (!c->batched)
+      PP_CUDA(launch_finalize(grid_for(c, c->n_terms, 4), c->stream, desc_of(c, d), c->d_ctl,
+                              c->cfg.coeff_eps));
+    c->launches += 30;
+  } else if (c->batched) {
     // FP64 accumulation rows, rounded to the storage type by the finalize pass
     double* acc = nullptr;
     const size_t acc_bytes = (size_t)std::max<uint64_t>(c->n_terms, 1) * c->B * sizeof(double);
@@ -442,9 +520,17 @@ pp_status queue_merge(pp_ctx* c, int group) {
   PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
   PP_CUDA(launch_ctl_insert(c->stream, c->d_ctl, 0, 1));
   const int grid = c->sms * 8;  // grid-stride; the count is on the device
-  PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid, c->stream, s.keys, s.coef, 0,
-                              &c->d_ctl->n_terms, c->cfg.coeff_eps > 0.0 ? 1 : 0, desc_of(c, d),
-                              c->d_ctl, 1));
+  if (sort_merge_ready(c, s.cap)) {
+    // the entry count is on the device; the table's capacity bounds it
+    PP_CUDA(launch_merge_sorted(group, c->n, -1, c->stream, s.keys, s.coef, nullptr, 0, nullptr,
+                                s.cap, &c->d_ctl->n_terms, c->cfg.coeff_eps > 0.0 ? 1 : 0,
+                                desc_of(c, d), 1, c->cfg.coeff_eps, c->d_ctl, c->sort_scratch, 1));
+    c->launches += 29;
+  } else {
+    PP_CUDA(launch_merge_insert(c->W, group, c->n, -1, grid, c->stream, s.keys, s.coef, 0,
+                                &c->d_ctl->n_terms, c->cfg.coeff_eps > 0.0 ? 1 : 0,
+                                desc_of(c, d), c->d_ctl, 1));
+  }
   PP_CUDA(launch_finalize(grid, c->stream, desc_of(c, d), c->d_ctl, c->cfg.coeff_eps, 1));
   PP_CUDA(launch_ctl_commit(c->stream, c->d_ctl, 1));
   c->launches += 4;
@@ -586,6 +672,9 @@ pp_status validate_config(const pp_config* cfg) {
     return fail(PP_ERR_ARG, "unknown noise mode");
   if (cfg->noise_mode != PP_NOISE_NONE && !(cfg->noise_p >= 0.0))
     return fail(PP_ERR_ARG, "noise_p must be >= 0");
+  if (cfg->merge_method != PP_MERGE_HASH && cfg->merge_method != PP_MERGE_SORT)
+    return fail(PP_ERR_ARG, "unknown merge_method");
+  if (cfg->wait_limit < 0) return fail(PP_ERR_ARG, "wait_limit must be >= 0");
   return PP_OK;
 }
 
@@ -774,6 +863,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
       return cleanup(fail(PP_ERR_CUDA, "constant table upload failed"));
     DevCtl zero;
     memset(&zero, 0, sizeof(zero));
+    zero.wait_limit = (unsigned)cfg->wait_limit;  // 0: the kernels' default bound
     if (upload(c, c->d_ctl, &zero, sizeof(zero)) != cudaSuccess)
       return cleanup(fail(PP_ERR_CUDA, "control block init failed"));
   }
@@ -1201,6 +1291,13 @@ pp_status pp_config_default(pp_config* cfg) {
   cfg->use_graphs = 1;
   cfg->profile_kernels = 0;
   cfg->layer_kernel = 1;
+  cfg->merge_method = PP_MERGE_HASH;
+  cfg->wait_limit = 0;
+  return PP_OK;
+}
+
+pp_status pp_debug_fail_alloc_after(int64_t n) {
+  g_fail_alloc_after.store(n < 0 ? -1 : (long long)n);
   return PP_OK;
 }
 
@@ -1237,6 +1334,7 @@ pp_status pp_destroy(pp_ctx* c) {
     if (e) cudaEventDestroy(e);
   free_buf(c, c->buf[0]);
   free_buf(c, c->buf[1]);
+  dfree(c, c->sort_scratch, c->sort_scratch_bytes);
   dfree(c, c->d_desc, 3 * sizeof(DevTable));
   dfree(c, c->d_ctl, sizeof(DevCtl));
   dfree(c, c->d_damp, sizeof(double) * (c->n + 1));
@@ -1349,8 +1447,11 @@ pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* t
   struct Counters {
     double updates;
     unsigned long long gates_done, ac_total;
-  } saved = {c->h_ctl->updates, c->h_ctl->gates_done, c->h_ctl->ac_total};
-  static_assert(offsetof(DevCtl, ac_total) - offsetof(DevCtl, updates) == 16,
+    double skipped_updates;
+    unsigned long long gates_skipped;
+  } saved = {c->h_ctl->updates, c->h_ctl->gates_done, c->h_ctl->ac_total,
+             c->h_ctl->skipped_updates, c->h_ctl->gates_skipped};
+  static_assert(offsetof(DevCtl, gates_skipped) - offsetof(DevCtl, updates) == 32,
                 "statistics counters are contiguous");
   const int64_t launches = c->launches, merges = c->merges, compactions = c->compactions,
                 regrows = c->regrows, timed = c->gates_timed;
@@ -1407,7 +1508,7 @@ pp_status pp_canonicalize(pp_ctx* c) {
   if (c->n_terms == 0) return PP_OK;
   Buf& b = c->buf[c->active];
   PP_CUDA(launch_canon_inplace(c->W, c->cfg.symmetry, c->n, grid_for(c, c->n_terms, 4), c->stream,
-                               b.keys, b.keys, c->n_terms));
+                               b.keys, b.keys, c->n_terms, c->d_ctl));
   c->launches += 1;
   c->merged = false;
   PP_CUDA(cudaStreamSynchronize(c->stream));
@@ -1510,8 +1611,9 @@ pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, doubl
   const int W = c->W;
   int spare = 1 - c->active;
   Buf& d = c->buf[spare];
-  // compact into the spare table without an index, then copy it out
-  PP_TRY(ctl_prepare_insert(c, 0));
+  // compact into the spare table without an index, then copy it out (the
+  // active table stays active, and so do its occupancy masks)
+  PP_TRY(ctl_prepare_insert(c, 0, false));
   if (c->batched) {
     PP_CUDA(launch_compact_batched(W, grid_for(c, c->n_terms, 4), c->stream,
                                    desc_of(c, c->buf[c->active]), c->n_terms, desc_of(c, d), 0,
@@ -1525,7 +1627,7 @@ pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, doubl
   PP_TRY(check_device_error(c));
   const int64_t m = (int64_t)c->h_ctl->n_next;
   // restore the control block of the live table
-  PP_TRY(ctl_prepare_insert(c, c->n_terms));
+  PP_TRY(ctl_prepare_insert(c, c->n_terms, false));
   {
     long long live = c->n_live;
     PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_live, &live, 8, cudaMemcpyHostToDevice, c->stream));
@@ -1576,6 +1678,8 @@ pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
   out->gate_kernel_ms = c->gate_ms;
   out->gate_kernels_timed = c->gates_timed;
   out->grid_scale = c->grid_scale;
+  out->skipped_updates = c->h_ctl->skipped_updates;
+  out->gates_skipped = (int64_t)c->h_ctl->gates_skipped;
   return PP_OK;
 }
 
@@ -1650,6 +1754,50 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
   cudaFreeAsync(index, s);
   cudaFreeAsync(ctl, s);
   if (e != cudaSuccess) return cuda_fail(e, "pp_merge_terms");
+  if (h.error) return fail(PP_ERR_INTERNAL, "device error in merge");
+  *m_out = (int64_t)h.n_next;
+  return PP_OK;
+}
+
+pp_status pp_merge_terms_sorted(int n_qubits, int symmetry, int64_t m, const uint64_t* keys_in,
+                                const double* coef_in, uint64_t* keys_out, double* coef_out,
+                                int64_t* m_out, void* stream) {
+  if (n_qubits < 1 || n_qubits > 64 * kMaxW) return fail(PP_ERR_ARG, "bad n_qubits");
+  if (!sort_merge_supported(n_qubits))
+    return fail(PP_ERR_ARG, "the sort-based merge takes n_qubits <= 64");
+  if (!valid_group(symmetry, n_qubits)) return fail(PP_ERR_ARG, "bad symmetry");
+  if (!m_out || m < 0 || (m > 0 && (!keys_in || !coef_in || !keys_out || !coef_out)))
+    return fail(PP_ERR_ARG, "bad arrays");
+  if ((uint64_t)m >= (1ull << 31)) return fail(PP_ERR_ARG, "too many terms");
+  *m_out = 0;
+  if (m == 0) return PP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t sbytes = sort_merge_scratch_bytes((uint64_t)m, n_qubits);
+  void* scratch = nullptr;
+  DevCtl* ctl = nullptr;
+  PP_CUDA(cudaMallocAsync(&scratch, sbytes, s));
+  cudaError_t e = cudaMallocAsync((void**)&ctl, sizeof(DevCtl), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch, s);
+    return cuda_fail(e, "cudaMallocAsync");
+  }
+  DevTable dst;
+  memset(&dst, 0, sizeof(dst));
+  dst.keys = keys_out;
+  dst.coef = coef_out;
+  dst.cap = (uint64_t)m;
+  DevCtl h;
+  memset(&h, 0, sizeof(h));
+  if ((e = cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s)) == cudaSuccess &&
+      (e = launch_merge_sorted(symmetry, n_qubits, -1, s, keys_in, coef_in, nullptr, 0, nullptr,
+                               (uint64_t)m, nullptr, 0, dst, 0, 0.0, ctl, scratch, 0)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(&h, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s)) == cudaSuccess) {
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFreeAsync(scratch, s);
+  cudaFreeAsync(ctl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pp_merge_terms_sorted");
   if (h.error) return fail(PP_ERR_INTERNAL, "device error in merge");
   *m_out = (int64_t)h.n_next;
   return PP_OK;

@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(kBlock)
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31;
   const int B = dst.B;
+  const unsigned wlimit = wait_limit_of(ctl);
   unsigned err = 0;
   unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
   const uint64_t wstride = (uint64_t)gridDim.x * kWarps;
@@ -310,8 +311,8 @@ __global__ void __launch_bounds__(kBlock)
             sv = old;
           }
           if ((uint32_t)(sv >> 32) == tag) {
-            int spins = 0;
-            while ((uint32_t)sv == kPendingIdx && spins < (1 << 22)) {
+            unsigned spins = 0;
+            while ((uint32_t)sv == kPendingIdx && spins < wlimit) {
               ++spins;
               __nanosleep(64);
               sv = *reinterpret_cast<volatile unsigned long long*>(index + pos);

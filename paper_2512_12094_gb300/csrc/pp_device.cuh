@@ -10,7 +10,22 @@ namespace {
 
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kSpinLimit = 1 << 22;
+// Default bound of a device wait (a grid barrier or a pending index slot):
+// 2^22 polls with a short sleep, well under a second on this GPU.  A context
+// may set another bound (DevCtl::wait_limit); a wait that runs out sets
+// kErrTimeout and returns, so the host reports PP_ERR_TIMEOUT.
+constexpr unsigned kDefaultWaitLimit = 1u << 22;
+// A merge queued behind a layer before the layer's outcome is known does
+// nothing when a gate of that layer stopped for capacity or failed.
+__device__ __forceinline__ bool queued_layer_stopped(const DevCtl* ctl) {
+  return *reinterpret_cast<const volatile unsigned*>(&ctl->stall) != 0u ||
+         *reinterpret_cast<const volatile unsigned*>(&ctl->error) != 0u;
+}
+
+__device__ __forceinline__ unsigned wait_limit_of(const DevCtl* ctl) {
+  const unsigned v = *reinterpret_cast<const volatile unsigned*>(&ctl->wait_limit);
+  return v ? v : kDefaultWaitLimit;
+}
 
 template <int W>
 struct Key {
@@ -131,6 +146,34 @@ __device__ __forceinline__ void index_claim(const DevTable& t, uint64_t pos, uin
   err |= kErrProbe;
 }
 
+// Accumulates the OR of keys in registers and adds it to a control block's
+// occupancy masks with one atomic per word and warp.
+template <int W>
+struct OccAcc {
+  uint64_t m[2 * W];
+  __device__ __forceinline__ OccAcc() {
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) m[j] = 0;
+  }
+  __device__ __forceinline__ void add(const Key<W>& k) {
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) m[j] |= k.w[j];
+  }
+  // every lane of the warp must call this
+  __device__ __forceinline__ void flush(DevCtl* ctl) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) {
+      uint64_t v = m[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+      // word j of the key is word (j % W) of x (j < W) or of z
+      const int slot = (j < W) ? j : (kMaxW + j - W);
+      if (lane == 0 && v) atomicOr(&ctl->occ[slot], (unsigned long long)v);
+    }
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -184,55 +227,8 @@ __device__ __forceinline__ uint64_t spread32(uint32_t a) {
   return x;
 }
 
-__device__ __forceinline__ uint32_t compact64(uint64_t x) {
-  x &= 0x5555555555555555ull;
-  x = (x | (x >> 1)) & 0x3333333333333333ull;
-  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
-  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
-  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
-  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
-  return (uint32_t)x;
-}
-
 __device__ __forceinline__ uint64_t digits32(uint32_t x, uint32_t z) {
   return spread32(x ^ z) | (spread32(z) << 1);
-}
-
-// Z_n (Algorithm 2): min over the n translations of the 2n-bit digit integer.
-// T^j moves the letter of qubit q+j to qubit q, i.e. rotates the integer
-// right by 2j bits inside 2n bits.
-__device__ __forceinline__ void canon_zn_w1(Key<1>& k, int n) {
-  const uint64_t x = k.x(0), z = k.z(0);
-  if (n <= 32) {
-    const int nb = 2 * n;
-    const uint64_t mask = (nb == 64) ? ~0ull : ((1ull << nb) - 1ull);
-    const uint64_t v = digits32((uint32_t)x, (uint32_t)z);
-    uint64_t best = v;
-    for (int j = 1; j < n; ++j) {
-      const uint64_t r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
-      best = r < best ? r : best;
-    }
-    const uint32_t zz = compact64(best >> 1);
-    const uint32_t xz = compact64(best);
-    k.x(0) = (uint64_t)(xz ^ zz);
-    k.z(0) = (uint64_t)zz;
-    return;
-  }
-  typedef unsigned __int128 u128;
-  const int nb = 2 * n;
-  const u128 mask = (nb == 128) ? ~(u128)0 : (((u128)1 << nb) - 1);
-  const u128 v = (u128)digits32((uint32_t)x, (uint32_t)z) |
-                 ((u128)digits32((uint32_t)(x >> 32), (uint32_t)(z >> 32)) << 64);
-  u128 best = v;
-  for (int j = 1; j < n; ++j) {
-    const u128 r = ((v >> (2 * j)) | (v << (nb - 2 * j))) & mask;
-    best = r < best ? r : best;
-  }
-  const uint64_t lo = (uint64_t)best, hi = (uint64_t)(best >> 64);
-  const uint64_t zz = (uint64_t)compact64(lo >> 1) | ((uint64_t)compact64(hi >> 1) << 32);
-  const uint64_t xz = (uint64_t)compact64(lo) | ((uint64_t)compact64(hi) << 32);
-  k.x(0) = xz ^ zz;
-  k.z(0) = zz;
 }
 
 template <int W>
@@ -242,36 +238,182 @@ __device__ __forceinline__ int digit_at(const Key<W>& k, int q) {
   return (zb << 1) | (xb ^ zb);
 }
 
-// Multi-word Z_n: compare translations digit by digit from the most
-// significant qubit and keep the smallest.
+// n-bit masks over W words (bits at or above n are zero).
 template <int W>
-__device__ __forceinline__ void canon_zn_generic(Key<W>& k, int n) {
-  int best = 0;
-  for (int j = 1; j < n; ++j) {
-    int cmp = 0;
-    for (int q = n - 1; q >= 0 && cmp == 0; --q) {
-      int qa = q + j;
-      qa -= (qa >= n) ? n : 0;
-      int qb = q + best;
-      qb -= (qb >= n) ? n : 0;
-      const int a = digit_at<W>(k, qa), b = digit_at<W>(k, qb);
-      cmp = (a < b) ? -1 : ((a > b) ? 1 : 0);
-    }
-    if (cmp < 0) best = j;
+struct Mask {
+  uint64_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Mask<W> nbits_mask(int n) {
+  Mask<W> m;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    const int b = n - 64 * i;
+    m.w[i] = b >= 64 ? ~0ull : (b > 0 ? ((1ull << b) - 1ull) : 0ull);
   }
-  if (best == 0) return;
+  return m;
+}
+
+// Logical shifts of a W-word value by s bits (0 <= s < 64 W); words are
+// picked with compile-time indices only, so nothing spills to local memory.
+template <int W>
+__device__ __forceinline__ Mask<W> mask_shr(const Mask<W>& v, int s) {
+  Mask<W> o;
+  const int ws = s >> 6, bs = s & 63;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    uint64_t lo = 0, hi = 0;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      lo = (t == i + ws) ? v.w[t] : lo;
+      hi = (t == i + ws + 1) ? v.w[t] : hi;
+    }
+    o.w[i] = bs ? ((lo >> bs) | (hi << (64 - bs))) : lo;
+  }
+  return o;
+}
+
+template <int W>
+__device__ __forceinline__ Mask<W> mask_shl(const Mask<W>& v, int s) {
+  Mask<W> o;
+  const int ws = s >> 6, bs = s & 63;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    uint64_t lo = 0, hi = 0;
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      hi = (t == i - ws) ? v.w[t] : hi;
+      lo = (t == i - ws - 1) ? v.w[t] : lo;
+    }
+    o.w[i] = bs ? ((hi << bs) | (lo >> (64 - bs))) : hi;
+  }
+  return o;
+}
+
+// Cyclic shift of an n-bit mask toward bit 0: bit q of the result is bit
+// (q + j) mod n of v (0 <= j < n).  This is the translation T^j of the
+// paper's example (T moves the letter of qubit q + 1 to qubit q).
+template <int W>
+__device__ __forceinline__ Mask<W> mask_rot(const Mask<W>& v, int j, int n, const Mask<W>& nm) {
+  if (j == 0) return v;
+  if constexpr (W == 1) {
+    Mask<1> o;
+    o.w[0] = ((v.w[0] >> j) | (v.w[0] << (n - j))) & nm.w[0];
+    return o;
+  } else {
+    const Mask<W> a = mask_shr<W>(v, j), b = mask_shl<W>(v, n - j);
+    Mask<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = (a.w[i] | b.w[i]) & nm.w[i];
+    return o;
+  }
+}
+
+template <int W>
+__device__ __forceinline__ bool mask_any(const Mask<W>& v) {
+  uint64_t a = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) a |= v.w[i];
+  return a != 0;
+}
+
+template <int W>
+__device__ __forceinline__ Key<W> rotate_key(const Key<W>& k, int j, int n, const Mask<W>& nm) {
+  Mask<W> x, z;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    x.w[i] = k.x(i);
+    z.w[i] = k.z(i);
+  }
+  x = mask_rot<W>(x, j, n, nm);
+  z = mask_rot<W>(z, j, n, nm);
   Key<W> r;
 #pragma unroll
-  for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
-  for (int q = 0; q < n; ++q) {
-    int src = q + best;
-    src -= (src >= n) ? n : 0;
-    const uint64_t xb = (k.x(src >> 6) >> (src & 63)) & 1ull;
-    const uint64_t zb = (k.z(src >> 6) >> (src & 63)) & 1ull;
-    r.x(q >> 6) |= xb << (q & 63);
-    r.z(q >> 6) |= zb << (q & 63);
+  for (int i = 0; i < W; ++i) {
+    r.x(i) = x.w[i];
+    r.z(i) = z.w[i];
   }
-  k = r;
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ bool key_less(const Key<W>& a, const Key<W>& b);
+
+// Z_n (Algorithm 2): the translation with the lowest digit integer.  Instead
+// of comparing all n translations, the search keeps only those that can be
+// lowest: the top digit of the lowest one is the smallest digit d present,
+// and the longer the run of d at the top, the lower the integer (a shorter
+// run is followed by a larger digit).  So the candidates put a longest
+// cyclic run of d on qubits n-L..n-1.  Bit p of M_L marks a window
+// p..p+L-1 (cyclic) of d's; M_{2^k} comes from doubling
+// (M_{2a} = M_a & T^a M_a) and the longest L from binary lifting over those,
+// in O(log n) mask operations.  The (usually one) candidates are then
+// compared as digit integers.  Equal to the exhaustive search by
+// construction; tested bit for bit against the oracle's enumeration.
+template <int W>
+__device__ __forceinline__ void canon_zn(Key<W>& k, int n) {
+  const Mask<W> nm = nbits_mask<W>(n);
+  Mask<W> sup, dm;
+  bool any_i = false, any_x = false, any_y = false;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    sup.w[i] = k.x(i) | k.z(i);
+    any_i |= (~sup.w[i] & nm.w[i]) != 0;
+    any_x |= (k.x(i) & ~k.z(i)) != 0;
+    any_y |= (k.x(i) & k.z(i)) != 0;
+  }
+  // mask of the smallest digit present: I, else X, else Y, else Z
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    dm.w[i] = any_i ? (~sup.w[i] & nm.w[i])
+                    : (any_x ? (k.x(i) & ~k.z(i)) : (any_y ? (k.x(i) & k.z(i)) : (k.z(i) & ~k.x(i))));
+  }
+  constexpr int kMaxK = (W == 1) ? 6 : (W == 2 ? 7 : 8);  // 2^(kMaxK+1) > 64 W >= n
+  Mask<W> M[kMaxK + 1];
+  M[0] = dm;
+  int K = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxK; ++t) {
+    if ((2 << t) <= n) {
+      const Mask<W> r = mask_rot<W>(M[t], 1 << t, n, nm);
+#pragma unroll
+      for (int i = 0; i < W; ++i) M[t + 1].w[i] = M[t].w[i] & r.w[i];
+      K = t + 1;
+    }
+  }
+  Mask<W> cur = nm;  // windows of length 0: every position
+  int L = 0;
+#pragma unroll
+  for (int t = kMaxK; t >= 0; --t) {
+    if (t <= K && L + (1 << t) <= n) {
+      const Mask<W> r = mask_rot<W>(M[t], L, n, nm);
+      Mask<W> c;
+#pragma unroll
+      for (int i = 0; i < W; ++i) c.w[i] = cur.w[i] & r.w[i];
+      if (mask_any<W>(c)) {
+        cur = c;
+        L += 1 << t;
+      }
+    }
+  }
+  if (L >= n) return;  // one letter everywhere: every translation is the same string
+  Key<W> best = k;
+  bool first = true;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    uint64_t m = cur.w[i];
+    while (m) {
+      const int p = 64 * i + __ffsll((long long)m) - 1;
+      m &= m - 1;
+      int j = p + L;
+      j -= (j >= n) ? n : 0;
+      const Key<W> r = rotate_key<W>(k, j, n, nm);
+      if (first || key_less<W>(r, best)) best = r;
+      first = false;
+    }
+  }
+  k = best;
 }
 
 __device__ __forceinline__ uint64_t range_word(int w, int lo, int hi) {
@@ -298,15 +440,6 @@ __device__ __forceinline__ void canon_sn(Key<W>& k) {
   for (int j = 0; j < W; ++j) {
     k.z(j) = range_word(j, 0, nz + ny);
     k.x(j) = range_word(j, nz, nz + ny + nx);
-  }
-}
-
-template <int W>
-__device__ __forceinline__ void canon_zn(Key<W>& k, int n) {
-  if constexpr (W == 1) {
-    canon_zn_w1(k, n);
-  } else {
-    canon_zn_generic<W>(k, n);
   }
 }
 

@@ -57,7 +57,7 @@ struct alignas(128) DevCtl {
   unsigned int stall;          // 1 + id of a gate that found too little capacity; 0 = none
   unsigned int first_gate;     // gates with a smaller layer-local id skip themselves
   unsigned int error;          // error bits (any kernel)
-  unsigned int pad0;
+  unsigned int wait_limit;     // iterations a bounded device wait may spin; 0 = the default
   alignas(128) unsigned long long base[3];  // stored entries entering the gate of a slot
   long long live_base[3];                   // live entries entering the gate of a slot
   alignas(128) unsigned long long cnt[3];   // births appended by the gate of a slot
@@ -65,6 +65,12 @@ struct alignas(128) DevCtl {
   alignas(128) double updates;              // sum of live terms entering each gate
   unsigned long long gates_done;
   unsigned long long ac_total;              // sum of live anticommuting terms per gate
+  double skipped_updates;                   // live terms entering gates the occupancy test skipped
+  unsigned long long gates_skipped;
+  // OR of the x words and of the z words of every stored string (a superset
+  // is allowed): a gate P with (x_P & occ_z) | (z_P & occ_x) == 0 commutes
+  // with every string, so the layer kernel skips it without a scan.
+  alignas(128) unsigned long long occ[2 * kMaxW];
   alignas(128) unsigned long long n_next;   // append cursor of merge / compaction kernels
   alignas(128) unsigned int bar_root;       // grid-barrier counter of the cooperative layer
                                             // kernel (grows by gridDim per barrier)
@@ -103,9 +109,11 @@ struct OverlapArgs {
 // n_live), counters of slot first%3 cleared, stall cleared.
 cudaError_t launch_chain_init(cudaStream_t s, DevCtl* ctl, unsigned first_gate);
 // Before a merge or compaction into a fresh table: append cursor n_next <-
-// first_free, live count <- 0 (stream ordered, no host round trip).
+// first_free, live count <- 0, and with reset_occ the occupancy masks <- 0
+// (the kernels that fill the table OR its keys back in).  Stream ordered, no
+// host round trip.
 cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free,
-                              int guarded = 0);
+                              int guarded = 0, int reset_occ = 1);
 // n_terms <- n_next (after a merge or compaction); guarded as above.
 cudaError_t launch_ctl_commit(cudaStream_t s, DevCtl* ctl, int guarded);
 // After the gates of a layer (n_gates of them): (n_terms, n_live) <- the state
@@ -134,8 +142,9 @@ cudaError_t launch_merge_insert(int W, int group, int n, int wmax, int grid, cud
                                 int skip_zero, DevTable dst, DevCtl* ctl, int guarded = 0);
 
 // Coefficient truncation (eps > 0) of dst entries [0, ctl->n_next); adds the
-// live count to ctl->n_live.  guarded: do nothing if ctl->stall is set (a
-// merge queued behind a layer that may have stopped for capacity).
+// live count to ctl->n_live.  guarded: do nothing if ctl->stall or
+// ctl->error is set (a merge queued behind a layer that may have stopped for
+// capacity or failed).
 cudaError_t launch_finalize(int grid, cudaStream_t s, DevTable dst, DevCtl* ctl, double eps,
                             int guarded = 0);
 
@@ -147,9 +156,11 @@ cudaError_t launch_compact(int W, int grid, cudaStream_t s, DevTable src, uint64
                            DevTable dst, int with_index, double eps, double extra_eps,
                            int extra_wmax, DevCtl* ctl);
 
-// keys[i] = representative of keys_in[i] (keys may equal keys_in).
+// keys[i] = representative of keys_in[i] (keys may equal keys_in); with ctl,
+// the representatives are ORed into its occupancy masks.
 cudaError_t launch_canon_inplace(int W, int group, int n, int grid, cudaStream_t s,
-                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count);
+                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count,
+                                 DevCtl* ctl = nullptr);
 
 // c <- c * table[weight(Q)] then coefficient truncation, over [0, n_terms);
 // adds the change of the live count to ctl->n_live.
@@ -201,6 +212,27 @@ cudaError_t launch_overlap_batched(int W, int grid, cudaStream_t s, DevTable t, 
 // rows (any element type) -> doubles [count][B] (export)
 cudaError_t launch_rows_to_double(int grid, cudaStream_t s, DevTable t, uint64_t count,
                                   double* out);
+
+// ------------------------------------------------------ sort-based merge
+// The merge of launch_merge_insert / launch_merge_batched done as an LSD radix
+// sort of the representatives (exact keys; n <= 64, one word per mask) and a
+// segmented FP64 reduce in input order (deterministic sums).  Single column:
+// src_coef != nullptr (entries equal to +0.0 skipped when skip_zero); batched:
+// src_coef == nullptr, src_rows / src_f32 / src_alive describe the source rows
+// and the reduce also writes liveness by the any-column rule under eps and adds
+// the live count (no finalize pass needed).  The distinct keys go to dst from
+// ctl->n_next on, which is advanced; with_index: they are also inserted into
+// dst's (clear) index.  scratch: sort_merge_scratch_bytes(count, n) bytes;
+// count is an upper bound when count_dev is given.  guarded as above.
+bool sort_merge_supported(int n);
+size_t sort_merge_scratch_bytes(uint64_t count, int n);
+cudaError_t launch_merge_sorted(int group, int n, int wmax, cudaStream_t s,
+                                const uint64_t* src_keys, const double* src_coef,
+                                const void* src_rows, int src_f32,
+                                const unsigned char* src_alive, uint64_t count,
+                                const unsigned long long* count_dev, int skip_zero, DevTable dst,
+                                int with_index, double eps, DevCtl* ctl, void* scratch,
+                                int guarded);
 
 int device_sm_count();
 int gate_blocks_per_sm(int W);  // resident gate-kernel blocks per SM

@@ -343,6 +343,12 @@ __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict
       ctl->dlt[next] = 0;
       atomicAdd(&ctl->updates, (double)L0);
       atomicAdd(&ctl->gates_done, 1ull);
+      // births R = Q xor P add at most P's letters to the occupancy masks
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        if (g.px[j]) atomicOr(&ctl->occ[j], (unsigned long long)g.px[j]);
+        if (g.pz[j]) atomicOr(&ctl->occ[kMaxW + j], (unsigned long long)g.pz[j]);
+      }
     }
     sh.nstage = 0;
     sh.err = 0;
@@ -362,8 +368,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-constexpr unsigned kBarrierSpinLimit = 1u << 24;
-
 // Grid-wide barrier of a cooperative launch (all blocks co-resident): every
 // block adds 1 to a counter that only grows during the launch (release) and
 // waits until it reaches (barrier number) x (blocks) (acquire).  The wait is
@@ -372,7 +376,8 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_ok) {
+__device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_ok,
+                                          unsigned limit) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
@@ -380,7 +385,7 @@ __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_
     red_release_add(&ctl->bar_root, 1u);
     unsigned spins = 0;
     while ((int)(ld_acquire_u32(&ctl->bar_root) - target) < 0) {
-      if (++spins > kBarrierSpinLimit) {
+      if (++spins > limit) {
         ok = 0;
         atomicOr(&ctl->error, kErrTimeout);
         break;
@@ -395,8 +400,19 @@ __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_
 
 // All gates of a layer in one cooperative launch: the table size travels in
 // registers and consecutive gates are separated by a grid barrier instead of
-// a kernel boundary.  Gate ids, slots and the capacity stall are the same as
-// for gate_kernel, so chain_init / chain_finish serve both.
+// a kernel boundary.  Gate ids and the capacity stall are the same as for
+// gate_kernel, so chain_init / chain_finish serve both: on leaving, block 0
+// records the table size where chain_finish reads it.
+//
+// Occupancy test: every block keeps the OR of the x and of the z words of all
+// stored strings (read from the control block, then widened by the letters
+// of each gate it applies, since a birth Q xor P only adds P's letters).  A
+// gate whose generator meets no letter that anticommutes with it -- and, with
+// per-gate noise, no letter on its support at all -- leaves every string as
+// it is; all blocks reach the same decision, so they skip it without a scan
+// or a barrier.  Its updates are counted as for any other gate (and, apart,
+// as skipped).  Executed gates take the counter slots by their ordinal e in
+// this launch.
 template <int W>
 __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
     layer_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
@@ -411,7 +427,14 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
   const int q0 = (int)((first + 2u) % 3u);
   unsigned long long T0 = __ldcg(&ctl->base[q0]) + __ldcg(&ctl->cnt[q0]);
   long long L0 = __ldcg(&ctl->live_base[q0]) + __ldcg(&ctl->dlt[q0]);
+  uint64_t ox[W], oz[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ox[j] = __ldcg(&ctl->occ[j]);
+    oz[j] = __ldcg(&ctl->occ[kMaxW + j]);
+  }
   unsigned target = 0;  // barrier counter value to wait for (cleared by chain_init)
+  const unsigned wlimit = wait_limit_of(ctl);
   if (threadIdx.x == 0) {
     sh.nstage = 0;
     sh.err = 0;
@@ -423,58 +446,99 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
   };
   if (__ldcg(&ctl->stall) != 0u || __ldcg(&ctl->error) != 0u) return;  // uniform
   if (first < n_gates) fetch_args(first, 0);
-  for (unsigned gid = first; gid < n_gates; ++gid) {
-    const int slot = (int)(gid % 3u), next = (int)((gid + 1u) % 3u);
-    const int buf = (int)((gid - first) & 1u);
+  unsigned e = 0;  // gates executed by this launch
+  int buf = 0;
+  unsigned end = n_gates;  // first gate not applied
+  for (unsigned gid = first; gid < n_gates; ++gid, buf ^= 1) {
+    __syncthreads();  // s_gate[buf] complete; the other buffer is free
+    const GateArgs& g = s_gate[buf];
+    uint64_t touch = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      touch |= (g.px[j] & oz[j]) | (g.pz[j] & ox[j]);
+      if (g.damp) touch |= g.supp[j] & (ox[j] | oz[j]);
+    }
+    if (touch == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(&ctl->updates, (double)L0);
+        atomicAdd(&ctl->gates_done, 1ull);
+        atomicAdd(&ctl->skipped_updates, (double)L0);
+        atomicAdd(&ctl->gates_skipped, 1ull);
+      }
+      if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);
+      continue;
+    }
     if (2ull * T0 > t.cap) {  // the same decision in every block
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->stall = gid + 1;
+      end = gid;
       break;
     }
+    const int slot = (int)(e % 3u), next = (int)((e + 1u) % 3u);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctl->base[slot] = T0;
-      ctl->live_base[slot] = L0;
       ctl->cnt[next] = 0;
       ctl->dlt[next] = 0;
       atomicAdd(&ctl->updates, (double)L0);
       atomicAdd(&ctl->gates_done, 1ull);
     }
-    __syncthreads();  // s_gate[buf] complete
-    gate_pass<W>(t, ctl, s_gate[buf], T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
+    gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      ox[j] |= g.px[j];
+      oz[j] |= g.pz[j];
+    }
     if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);  // overlaps the barrier wait
     if (gridDim.x == 1) {
       // a small table in one block: its own writes and atomics, ordered by a
       // fence and the block barrier, are all the next gate depends on
       __threadfence();
       __syncthreads();
-    } else if (!grid_sync(ctl, target, s_ok)) {
+    } else if (!grid_sync(ctl, target, s_ok, wlimit)) {
       return;
     }
     T0 += __ldcg(&ctl->cnt[slot]);
     L0 += __ldcg(&ctl->dlt[slot]);
+    ++e;
     if (__ldcg(&ctl->error) != 0u) return;  // uniform after the barrier
+  }
+  // the state after the last gate applied, where chain_finish looks for it
+  // (slot of gate end - 1), and the widened occupancy masks
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int q = (int)((end + 2u) % 3u);
+    ctl->base[q] = T0;
+    ctl->cnt[q] = 0;
+    ctl->live_base[q] = L0;
+    ctl->dlt[q] = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      ctl->occ[j] = ox[j];
+      ctl->occ[kMaxW + j] = oz[j];
+    }
   }
 }
 
-__global__ void ctl_insert_kernel(DevCtl* ctl, unsigned long long first_free, int guarded) {
-  if (guarded && ctl->stall != 0u) return;
+__global__ void ctl_insert_kernel(DevCtl* ctl, unsigned long long first_free, int guarded,
+                                  int reset_occ) {
+  if (guarded && queued_layer_stopped(ctl)) return;
   ctl->n_next = first_free;
   ctl->n_live = 0;
+  if (reset_occ)
+    for (int j = 0; j < 2 * kMaxW; ++j) ctl->occ[j] = 0ull;
 }
 
 __global__ void ctl_commit_kernel(DevCtl* ctl, int guarded) {
-  if (guarded && ctl->stall != 0u) return;
+  if (guarded && queued_layer_stopped(ctl)) return;
   ctl->n_terms = ctl->n_next;
 }
 
 __global__ void chain_init_kernel(DevCtl* ctl, unsigned first_gate) {
-  const int q = (int)((first_gate + 2u) % 3u), p = (int)(first_gate % 3u);
+  const int q = (int)((first_gate + 2u) % 3u);
   ctl->bar_root = 0;
   ctl->base[q] = ctl->n_terms;
   ctl->live_base[q] = ctl->n_live;
-  ctl->cnt[q] = 0;
-  ctl->dlt[q] = 0;
-  ctl->cnt[p] = 0;
-  ctl->dlt[p] = 0;
+  for (int k = 0; k < 3; ++k) {
+    ctl->cnt[k] = 0;
+    ctl->dlt[k] = 0;
+  }
   ctl->stall = 0;
   ctl->first_gate = first_gate;
 }
@@ -495,9 +559,11 @@ __global__ void __launch_bounds__(kBlock)
                         int wmax, int n, int lx, DevTable dst, DevCtl* ctl, int guarded) {
   // guarded: queued behind a layer before its outcome is known; nothing to
   // do if that layer stopped for capacity
-  if (guarded && *reinterpret_cast<volatile unsigned*>(&ctl->stall) != 0u) return;
+  if (guarded && queued_layer_stopped(ctl)) return;
   const uint64_t T = count_dev ? *count_dev : count;
+  const unsigned wlimit = wait_limit_of(ctl);
   unsigned err = 0;
+  OccAcc<W> occ;
   unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T; i += stride) {
@@ -506,6 +572,7 @@ __global__ void __launch_bounds__(kBlock)
     Key<W> K = ld_key<W>(src_keys, i);
     if (wmax >= 0 && weight(K) > wmax) continue;
     canon<W, G>(K, n, lx);
+    occ.add(K);
     const uint64_t h = key_hash(K);
     const uint32_t tag = tag_of(h);
     uint64_t pos = h & dst.imask;
@@ -535,8 +602,8 @@ __global__ void __launch_bounds__(kBlock)
         s = old;
       }
       if ((uint32_t)(s >> 32) == tag) {
-        int spins = 0;
-        while ((uint32_t)s == kPendingIdx && spins < kSpinLimit) {
+        unsigned spins = 0;
+        while ((uint32_t)s == kPendingIdx && spins < wlimit) {
           ++spins;
           __nanosleep(64);
           s = *reinterpret_cast<volatile unsigned long long*>(index + pos);
@@ -557,6 +624,7 @@ __global__ void __launch_bounds__(kBlock)
     }
     if (!done) err |= kErrProbe;
   }
+  occ.flush(ctl);
   if (err) atomicOr(&ctl->error, err);
 }
 
@@ -564,7 +632,7 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock) finalize_kernel(DevTable t, DevCtl* ctl, double eps,
                                                          int guarded) {
   __shared__ long long s_live[kBlock / 32];
-  if (guarded && *reinterpret_cast<volatile unsigned*>(&ctl->stall) != 0u) return;
+  if (guarded && queued_layer_stopped(ctl)) return;
   const uint64_t T = *reinterpret_cast<volatile unsigned long long*>(&ctl->n_next);
   long long live = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -599,6 +667,7 @@ __global__ void __launch_bounds__(kBlock)
   const int lane = threadIdx.x & 31;
   unsigned err = 0;
   long long live = 0;
+  OccAcc<W> occ;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count;
        base += stride) {
@@ -628,6 +697,7 @@ __global__ void __launch_bounds__(kBlock)
         } else {
           st_key<W>(dst.keys, idx, K);
           dst.coef[idx] = c;
+          occ.add(K);
           ++live;
           if (with_index) {
             const uint64_t h = key_hash(K);
@@ -639,18 +709,23 @@ __global__ void __launch_bounds__(kBlock)
   }
   live = warp_sum(live);
   if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live), (unsigned long long)live);
+  occ.flush(ctl);
   if (err) atomicOr(&ctl->error, err);
 }
 
 template <int W, int G>
 __global__ void __launch_bounds__(kBlock)
-    canon_inplace_kernel(uint64_t* keys, const uint64_t* keys_in, uint64_t count, int n, int lx) {
+    canon_inplace_kernel(uint64_t* keys, const uint64_t* keys_in, uint64_t count, int n, int lx,
+                         DevCtl* ctl) {
+  OccAcc<W> occ;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     Key<W> k = ld_key_cg<W>(keys_in, i);
     canon<W, G>(k, n, lx);
     st_key<W>(keys, i, k);
+    occ.add(k);
   }
+  if (ctl) occ.flush(ctl);
 }
 
 template <int W>
@@ -801,8 +876,8 @@ __global__ void __launch_bounds__(kBlock)
   }
 
 cudaError_t launch_ctl_insert(cudaStream_t s, DevCtl* ctl, unsigned long long first_free,
-                              int guarded) {
-  ctl_insert_kernel<<<1, 1, 0, s>>>(ctl, first_free, guarded);
+                              int guarded, int reset_occ) {
+  ctl_insert_kernel<<<1, 1, 0, s>>>(ctl, first_free, guarded, reset_occ);
   return cudaGetLastError();
 }
 
@@ -923,10 +998,12 @@ cudaError_t launch_compact(int W, int grid, cudaStream_t s, DevTable src, uint64
 }
 
 cudaError_t launch_canon_inplace(int W, int group, int n, int grid, cudaStream_t s,
-                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count) {
+                                 uint64_t* keys, const uint64_t* keys_in, uint64_t count,
+                                 DevCtl* ctl) {
   const int lx = group >> 8;
 #define PP_CANON_G(GG) \
-  PP_DISPATCH_W(W, (canon_inplace_kernel<WW, GG><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n, lx)))
+  PP_DISPATCH_W(W, (canon_inplace_kernel<WW, GG><<<grid, kBlock, 0, s>>>(keys, keys_in, count, n, \
+                                                                        lx, ctl)))
   switch (group & 0xFF) {
     case 1: PP_CANON_G(1); break;
     case 2: PP_CANON_G(2); break;

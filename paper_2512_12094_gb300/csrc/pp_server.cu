@@ -7,12 +7,26 @@
 // arrives while others run starts as soon as a slot and memory are free, and
 // the kernels of different jobs overlap on the device.  A job runs in its own
 // context (tables resident on the device for its whole life) whose memory
-// budget is its reservation; if the job outgrows it (PP_ERR_CAPACITY) it is put
-// back at the head of the queue with four times the reservation, up to the
-// server budget.  Every job's result depends only on the job: contexts share
-// nothing, and per-job work is the same as a single pp_create /
-// pp_apply_layer / pp_expect sequence.
+// budget is its reservation.
+//
+// Reservations follow the jobs' live-term counts.  A job's first reservation
+// is the memory of a table for its observable (unless the job names one).
+// Between layers the worker compares the context's device memory, scaled by
+// the growth of the live-term count over the last layer, with the
+// reservation and asks the server for more before the next layer; a layer
+// that still runs out of room (PP_ERR_CAPACITY, the context restored to its
+// state before the layer) gets twice the reservation and is applied again.
+// The job never starts over.  A running job waiting for more memory has
+// priority over queued jobs; a queued job that younger jobs have passed
+// kMaxBypass times is passed no more.  If every running job waits for memory
+// the one that notices gives its memory back and is queued again at the head
+// with the reservation it asked for (the only case where work is repeated).
+// Every job's result depends only on the job: contexts share nothing, and
+// per-job work is the same as a single pp_create / pp_apply_layer / pp_expect
+// sequence.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +54,11 @@ struct Job {
   int n_layers = 0;
   int boundary = 1;
   size_t reserve = 0;
+  int grows = 0;     // reservation increases
+  int restarts = 0;  // times the job gave its memory back and started over
+  int bypassed = 0;  // younger jobs admitted while this one waited at the queue's head
+  size_t want_next = 0;  // reservation asked for when the job gave its memory back
+  bool started = false;
   std::chrono::steady_clock::time_point t_submit, t_start;
 };
 
@@ -59,6 +78,7 @@ struct pp_server {
   size_t budget = 0;
   size_t default_reserve = 0;
   size_t reserved = 0;  // sum of the reservations of running jobs
+  int64_t growing = 0;  // running jobs waiting for a larger reservation
   int device = 0;
   bool stopping = false;
   uint64_t next_id = 1;
@@ -73,29 +93,122 @@ struct pp_server {
 
 namespace {
 
-// Oldest queued job whose reservation fits; nullptr if none.
+constexpr int kMaxBypass = 8;
+constexpr size_t kMiB = (size_t)1 << 20;
+
+size_t round_mib(double b) { return ((size_t)std::ceil(b / (double)kMiB) + 1) * kMiB; }
+
+// Device memory of a context holding `terms` strings: two tables with room
+// for four times the terms (entries, coefficients and a hash index of at
+// least 1.5x the capacity), the dense copy kept while a layer runs, and a
+// megabyte of fixed buffers.
+size_t estimate_job_bytes(const pp_config& cfg, int64_t terms) {
+  const double W = (double)((cfg.n_qubits + 63) / 64);
+  const bool batched = cfg.batch > 1 || cfg.coef_type == PP_COEF_F32;
+  const double row = batched ? (double)cfg.batch * (cfg.coef_type == PP_COEF_F32 ? 4.0 : 8.0) + 1.0
+                             : 8.0;
+  const double cap = std::max<double>(4.0 * (double)terms, 1024.0);
+  const double table = cap * (16.0 * W + row) + 2.0 * cap * 8.0;
+  return round_mib(2.0 * table + (double)terms * (16.0 * W + row) + (double)kMiB);
+}
+
+// Oldest queued job whose reservation fits; nullptr if none.  Jobs waiting
+// to grow come first, and a job passed kMaxBypass times blocks younger ones.
 std::unique_ptr<Job> take_fitting(pp_server* s) {
+  if (s->growing > 0) return nullptr;
   for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
     if (s->reserved + (*it)->reserve <= s->budget) {
+      for (auto older = s->queue.begin(); older != it; ++older) (*older)->bypassed++;
       std::unique_ptr<Job> j = std::move(*it);
       s->queue.erase(it);
       return j;
     }
+    if ((*it)->bypassed >= kMaxBypass) return nullptr;
   }
   return nullptr;
 }
 
-// Run one job on `stream`: returns its status; fills r.
-pp_status run_job(const Job& j, cudaStream_t stream, pp_job_result& r) {
+enum class Grow { kGranted, kNever, kGiveBack };
+
+// Raise a running job's reservation to `want` (capped at the budget),
+// waiting for running jobs to free memory.  kNever: the job is at the budget
+// already; kGiveBack: every running job waits for memory, so this one must
+// release its own.
+Grow grow_reservation(pp_server* s, Job& j, size_t want) {
+  std::unique_lock<std::mutex> lock(s->mu);
+  want = std::min(want, s->budget);
+  if (want <= j.reserve) return Grow::kNever;
+  s->growing++;
+  for (;;) {
+    if (s->reserved - j.reserve + want <= s->budget) {
+      s->reserved += want - j.reserve;
+      j.reserve = want;
+      j.grows++;
+      s->growing--;
+      return Grow::kGranted;
+    }
+    if (s->growing >= s->running) {  // nobody can finish and free memory
+      s->growing--;
+      j.want_next = want;  // ask for this much when admitted again
+      return Grow::kGiveBack;
+    }
+    s->cv_work.wait(lock);
+  }
+}
+
+// Run one job on `stream`: returns its status; fills r.  *give_back is set
+// when the job released its memory to let others finish (it is queued
+// again).
+pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, bool* give_back) {
+  *give_back = false;
   pp_config cfg = j.cfg;
   cfg.cuda_stream = stream;
   cfg.mem_budget_bytes = j.reserve;
   cfg.layer_kernel = 0;  // one kernel per gate: jobs on other streams can interleave
   pp_ctx* ctx = nullptr;
-  pp_status st = pp_create(&cfg, (int64_t)j.coef.size() / cfg.batch, j.x.data(), j.z.data(),
-                           j.coef.data(), &ctx);
-  for (int l = 0; st == PP_OK && l < j.n_layers; ++l)
-    st = pp_apply_layer(ctx, (int)j.gates.size(), j.gates.data(), j.theta.data(), j.boundary);
+  // a reactive increase: twice the reservation; false when the job must stop
+  auto grow_or_stop = [&](pp_status& st) {
+    const Grow g = grow_reservation(s, j, 2 * j.reserve);
+    if (g == Grow::kGranted) {
+      if (ctx) pp_set_budget(ctx, j.reserve);
+      return true;
+    }
+    if (g == Grow::kGiveBack) *give_back = true;
+    (void)st;
+    return false;
+  };
+  pp_status st;
+  for (;;) {
+    cfg.mem_budget_bytes = j.reserve;
+    st = pp_create(&cfg, (int64_t)j.coef.size() / cfg.batch, j.x.data(), j.z.data(),
+                   j.coef.data(), &ctx);
+    if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
+  }
+  int64_t live_prev = -1;
+  for (int l = 0; st == PP_OK && l < j.n_layers; ++l) {
+    // proactive: the memory the context holds, scaled by the live-term
+    // growth of the last layer, should fit the reservation
+    pp_stats_t stats;
+    if (pp_stats(ctx, &stats) == PP_OK) {
+      const double growth =
+          live_prev > 0 ? std::max(1.0, (double)stats.live_terms / (double)live_prev) : 1.0;
+      const size_t predicted = round_mib((double)stats.device_bytes * std::min(growth, 16.0));
+      live_prev = stats.live_terms;
+      if (predicted > j.reserve) {
+        const Grow g = grow_reservation(s, j, predicted);
+        if (g == Grow::kGranted) pp_set_budget(ctx, j.reserve);
+        if (g == Grow::kGiveBack) {
+          *give_back = true;
+          st = PP_ERR_CAPACITY;
+          break;
+        }
+      }
+    }
+    for (;;) {
+      st = pp_apply_layer(ctx, (int)j.gates.size(), j.gates.data(), j.theta.data(), j.boundary);
+      if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
+    }
+  }
   if (st == PP_OK) st = pp_expect(ctx, j.bloch.data(), &r.value);
   if (st != PP_OK) snprintf(r.message, sizeof(r.message), "%s", pp_last_error());
   if (ctx) {
@@ -123,22 +236,27 @@ void worker_main(pp_server* s) {
       s->reserved += j->reserve;
       s->running++;
     }
-    j->t_start = Clock::now();
+    if (!j->started) {
+      j->t_start = Clock::now();
+      j->started = true;
+    }
     pp_job_result r;
     memset(&r, 0, sizeof(r));
     pp_status st = PP_ERR_CUDA;
+    bool give_back = false;
     if (have_stream) {
-      st = run_job(*j, stream, r);
+      st = run_job(s, *j, stream, r, &give_back);
     } else {
       snprintf(r.message, sizeof(r.message), "%s", "the worker could not create its CUDA stream");
     }
     const auto t_end = Clock::now();
     std::unique_lock<std::mutex> lock(s->mu);
-    s->reserved -= j->reserve;
+    s->reserved -= j->reserve;  // every granted increase was added to `reserved`
     s->running--;
-    if (st == PP_ERR_CAPACITY && j->reserve < s->budget) {
-      // grow the reservation and retry first
-      j->reserve = std::min(s->budget, j->reserve * 4);
+    if (give_back) {
+      j->reserve = j->want_next;
+      j->restarts++;
+      j->bypassed = 0;
       s->queue.push_front(std::move(j));
     } else {
       r.done = 1;
@@ -147,6 +265,8 @@ void worker_main(pp_server* s) {
       r.run_ms = ms_between(j->t_start, t_end);
       r.latency_ms = ms_between(j->t_submit, t_end);
       r.reserved_bytes = j->reserve;
+      r.grows = j->grows;
+      r.restarts = j->restarts;
       s->results[j->id].r = r;
       s->completed++;
       s->cv_done.notify_all();
@@ -168,7 +288,7 @@ pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_jo
   }
   pp_server* s = new pp_server();
   s->budget = mem_budget_bytes;
-  s->default_reserve = default_job_bytes ? default_job_bytes : ((size_t)64 << 20);
+  s->default_reserve = default_job_bytes;  // 0: each job's reservation is estimated
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     ppk::set_last_error("pp_server_create: no CUDA device");
@@ -203,7 +323,9 @@ pp_status pp_submit(pp_server* s, const pp_job* job, uint64_t* job_id) {
   j->bloch.assign(job->bloch, job->bloch + 3 * cfg.n_qubits);
   j->n_layers = job->n_layers;
   j->boundary = job->symmetric_boundary;
-  j->reserve = job->mem_bytes ? job->mem_bytes : s->default_reserve;
+  j->reserve = job->mem_bytes ? job->mem_bytes
+                              : (s->default_reserve ? s->default_reserve
+                                                    : estimate_job_bytes(cfg, job->n_terms));
   std::lock_guard<std::mutex> lock(s->mu);
   if (j->reserve > s->budget) {
     ppk::set_last_error("pp_submit: job reservation exceeds the server memory budget");

@@ -336,6 +336,32 @@ def xxz_all_to_all(n: int, delta_t: float, steps: int, J: float = 1.0, Delta: fl
                     noise_p=gamma, noise_mode=2 if gamma > 0 else 0, symmetry=symmetry)
 
 
+def split_sublayers(wl: Workload, parts: int = 3) -> Workload:
+    """The same workload with every layer cut into `parts` consecutive
+    sublayers of equal length, each applied as a layer of its own.  For the
+    ring layer these are all RZZ, all RX and all RZ gates: each is a set of
+    commuting gates mapped onto itself by the translations, so a merge may
+    follow any of them."""
+    layers = []
+    for layer in wl.circuit.layers:
+        if len(layer) % parts:
+            raise ValueError("layer length is not a multiple of parts")
+        k = len(layer) // parts
+        layers.extend([list(layer[i * k:(i + 1) * k]) for i in range(parts)])
+    return Workload(wl.name + "_sub%d" % parts, Circuit(wl.circuit.n, layers), wl.observable,
+                    wl.state, eps=wl.eps, max_weight=wl.max_weight, noise_p=wl.noise_p,
+                    noise_mode=wl.noise_mode, symmetry=wl.symmetry)
+
+
+def merge_schedule(n_layers: int, every: int) -> List[bool]:
+    """Merge flags in application order (the last layer of the circuit comes
+    first): a symmetry merge after every `every`-th applied layer and after the
+    final one."""
+    if every < 1:
+        raise ValueError("every must be >= 1")
+    return [((a + 1) % every == 0) or (a == n_layers - 1) for a in range(n_layers)]
+
+
 def torus_ising(lx: int, ly: int, steps: int, theta_j: float = 0.4, theta_x: float = 0.6,
                 theta_z: float = 0.3, eps: float = 0.0, max_weight: int = -1,
                 symmetry: int = 0) -> Workload:

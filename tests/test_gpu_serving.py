@@ -122,12 +122,77 @@ def test_oversized_job_is_rejected():
     pp.pp_server_destroy(server)
 
 
-def test_small_reservation_grows_and_retries():
+def test_reservation_grows_between_layers_without_restarting():
+    """A job admitted with far too small a reservation finishes: its
+    reservation is raised between layers (and a layer that runs out of room is
+    applied again from the state before it), never from the first layer."""
     wl = workload("ring", 32, 10, 1e-4, 3)
     server = pp.pp_server_create(2, 2 << 30, 0)
     job, bufs = job_of(wl, mem_bytes=128 << 10)  # less than the job's tables will need
     r = pp.pp_server_wait(server, pp.pp_submit(server, job))
     pp.pp_server_destroy(server)
-    assert r["status"] == 0
+    assert r["status"] == 0, r["message"]
     assert r["reserved_bytes"] > 128 << 10
+    assert r["grows"] >= 1 and r["restarts"] == 0
     assert r["value"] == pytest.approx(alone(wl), abs=1e-10)
+
+
+def test_estimated_reservation_from_the_observable():
+    """With no reservation named anywhere, a job is admitted with an estimate
+    from its observable's size and grows from there."""
+    wl = workload("ring", 24, 6, 1e-5, 4)
+    server = pp.pp_server_create(2, 2 << 30, 0)
+    job, bufs = job_of(wl)
+    r = pp.pp_server_wait(server, pp.pp_submit(server, job))
+    pp.pp_server_destroy(server)
+    assert r["status"] == 0, r["message"]
+    assert r["reserved_bytes"] >= 1 << 20 and r["restarts"] == 0
+    assert r["value"] == pytest.approx(alone(wl), abs=1e-10)
+
+
+def test_growing_job_is_not_starved_by_a_stream_of_small_jobs():
+    """One job that must grow to most of the budget competes with small jobs
+    that keep arriving: running jobs that wait for memory are served before
+    new admissions, so it finishes; every result equals the job alone and the
+    reservations never exceed the budget."""
+    big = workload("ring", 32, 8, 1e-5, 5)
+    p = pp.Propagator.from_workload(big, symmetry=1)
+    want_big = p.run(big)
+    big_bytes = p.stats()["device_bytes"]
+    p.close()
+    budget = int(2.5 * big_bytes) + (64 << 20)
+    small = [workload("ring", 12, 3, 1e-5, 100 + k) for k in range(40)]
+    server = pp.pp_server_create(4, budget, 0)
+    keep = []
+    job, bufs = job_of(big, mem_bytes=1 << 20)
+    keep.append(bufs)
+    big_id = pp.pp_submit(server, job)
+    ids = []
+    stop = threading.Event()
+    peak = [0]
+
+    def watch():
+        while not stop.is_set():
+            st = pp.pp_server_stats(server)
+            peak[0] = max(peak[0], st["reserved_bytes"])
+            time.sleep(0.0005)
+
+    w = threading.Thread(target=watch)
+    w.start()
+    for wl in small:
+        job, bufs = job_of(wl)
+        keep.append(bufs)
+        ids.append(pp.pp_submit(server, job))
+        time.sleep(0.002)
+    rb = pp.pp_server_wait(server, big_id)
+    rs = [pp.pp_server_wait(server, j) for j in ids]
+    stop.set()
+    w.join()
+    pp.pp_server_destroy(server)
+    assert rb["status"] == 0, rb["message"]
+    assert rb["grows"] >= 1
+    assert rb["value"] == pytest.approx(want_big, abs=1e-10)
+    assert peak[0] <= budget
+    for r, wl in zip(rs, small):
+        assert r["status"] == 0, r["message"]
+        assert r["value"] == pytest.approx(alone(wl), abs=1e-10)

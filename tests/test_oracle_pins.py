@@ -253,6 +253,37 @@ def test_theorem1_sn_merge_is_exact_on_symmetric_layer(oracle_lib, state):
     assert len(merged_st) <= math.comb(n + 3, 3)
 
 
+@pytest.mark.parametrize("every,sub", [(1, False), (2, False), (4, False), (1, True), (5, True)])
+def test_theorem1_any_merge_cadence_is_exact(oracle_lib, every, sub):
+    """Merging after every k-th symmetric layer (or after every RZZ / RX / RZ
+    sublayer) leaves <O> unchanged without truncation: each merge happens at a
+    boundary where the operator is invariant, so Theorem 1 applies at any
+    cadence.  Checked against the state vector."""
+    n, steps = 6, 4
+    wl = pi.config1_ring(n=n, steps=steps, eps=0.0, max_weight=-1)
+    run = pi.split_sublayers(wl) if sub else wl
+    L = len(run.circuit.layers)
+    flags = pi.merge_schedule(L, every)
+    ox, oz, oc = wl.observable.arrays()
+    st = oracle_lib.OracleState(n, ox, oz, oc, group=1)
+    for a, layer in enumerate(reversed(range(L))):
+        gx, gz, th = run.circuit.gate_arrays(layer)
+        st.apply_layer(gx, gz, th, group=1 if flags[a] else 0)
+    ref = sv.statevector_expectations(wl.circuit.layers, wl.observable.terms, wl.state.bloch)[-1]
+    assert st.expect(wl.state.bloch, 1) == pytest.approx(ref, abs=1e-12)
+
+
+def test_merge_schedule_and_sublayers():
+    assert pi.merge_schedule(5, 2) == [False, True, False, True, True]
+    assert pi.merge_schedule(3, 1) == [True, True, True]
+    wl = pi.config1_ring(n=5, steps=2)
+    sub = pi.split_sublayers(wl)
+    assert len(sub.circuit.layers) == 6
+    assert [g for layer in sub.circuit.layers for g in layer] == \
+        [g for layer in wl.circuit.layers for g in layer]
+    assert {s.replace("I", "") for s, _ in sub.circuit.layers[1]} == {"X"}
+
+
 def test_observation1_orbit_supported_operator_is_unchanged(oracle_lib):
     n = 5
     rng = np.random.default_rng(5)
