@@ -127,7 +127,8 @@ class ClockSampler:
 GROUPS = {"both": (0, 1), "plain": (0,), "zn": (1,)}
 
 
-def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, only="both"):
+def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, only="both",
+            block_threads=0):
     """One job: plain then Z_n-merged propagation of the whole circuit.
     marks: optional [event, event, event] recorded before, between, after."""
     n = wl.circuit.n
@@ -138,7 +139,7 @@ def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, o
             marks[gi].record(stream)
         cfg = pp.pp_config_default(n_qubits=n, symmetry=group, coeff_eps=wl.eps,
                                    max_weight=wl.max_weight, cuda_stream=stream,
-                                   profile_kernels=int(profile))
+                                   profile_kernels=int(profile), block_threads=block_threads)
         if host_inputs:
             ox, oz, oc = wl.observable.arrays()
             ctx = pp.pp_create(cfg, ox, oz, oc)
@@ -195,13 +196,14 @@ def bench_ours(args):
         if args.only != "both":
             ev[1] = ev[0]
         vals, stats = run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=ev,
-                              only=args.only)
+                              only=args.only, block_threads=args.block_threads)
         ev[2].synchronize()
         return vals, stats, ev
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            run_job(pp, wl, layers, obs_dev, stream, False, False, only=args.only)
+            run_job(pp, wl, layers, obs_dev, stream, False, False, only=args.only,
+                    block_threads=args.block_threads)
         barrier()
         clocks = ClockSampler(local)
         clocks.start()
@@ -229,12 +231,14 @@ def bench_ours(args):
         barrier()
         # roofline pass: the same jobs with CUDA events around every layer kernel
         # on the job's stream (separate from the timed regions above)
-        pupd = ac = gate_ms = 0.0
-        gate_n = 0
+        pupd = ac = gate_ms = skipped = 0.0
+        gate_n = gates_skipped = 0
         for _ in range(args.steps):
             _, pstats, _ = timed_job(False, True)
             for st in pstats:
                 pupd += st["gate_updates"]
+                skipped += st["skipped_updates"]
+                gates_skipped += st["gates_skipped"]
                 ac += st["anticommuting_terms"]
                 gate_ms += st["gate_kernel_ms"]
                 gate_n += st["gate_kernels_timed"]
@@ -244,7 +248,9 @@ def bench_ours(args):
     upd_per_rank = upd / args.steps  # one job's updates (the same on every rank)
     hbm, peak_kind = peaks()
     per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
-    bytes_alg = KEY_BYTES * pupd + per_ac * ac
+    # gates the occupancy test skipped read nothing: their updates count in the
+    # metric (every string is processed: it commutes) but add no bytes
+    bytes_alg = KEY_BYTES * (pupd - skipped) + per_ac * ac
     achieved = bytes_alg / (gate_ms / 1e3) / 1e9 if gate_ms > 0 else None
     gates_per_job = len(GROUPS[args.only]) * sum(len(l[1]) for l in layers)
     h2d = len(GROUPS[args.only]) * (ox.nbytes + oz.nbytes + oc.nbytes + wl.state.bloch.nbytes +
@@ -276,10 +282,15 @@ def bench_ours(args):
                      "traffic_basis": "ncu DRAM bytes per algorithmic byte of the last layer "
                                       "of the Z_32 job x this run's average launch; null when "
                                       "the kernel sources differ from the captured ones",
-                     "kernel": "layer_kernel<1>", "peak_kind": peak_kind,
+                     "kernel": "layer_kernel<1>", "block_threads": stats[-1]["block_threads"],
+                     "peak_kind": peak_kind,
                      "peak_nominal": HBM_NOMINAL_GBS,
                      "frac_nominal": (achieved / HBM_NOMINAL_GBS) if achieved else None,
-                     "bytes_model": "16 B key per live term + 64 B per live anticommuting term",
+                     "bytes_model": "16 B key per live term entering a scanned gate + 64 B per "
+                                    "live anticommuting term (gates skipped by the occupancy "
+                                    "test move no bytes)",
+                     "skipped_updates_fraction": (skipped / pupd) if pupd else None,
+                     "gates_skipped_per_job": gates_skipped / max(args.steps, 1),
                      "avg_launch_us": 1e3 * gate_ms / max(gate_n, 1),
                      "algorithmic_bytes_per_launch": bytes_alg / max(gate_n, 1),
                      "timing": "CUDA events around every layer kernel, in a pass of the "
@@ -404,27 +415,56 @@ def serving_specs(n_jobs, rate, seed=0):
     return out
 
 
+def serving_specs_full(n_jobs, rate, seed=0):
+    """The serving workload at its stated sizes: the first n_jobs of the seeded
+    2000-job Poisson stream.  Ring jobs are the translation-symmetric ring
+    circuit with the job's three angles, Pauli weight <= 10, (1/n) sum Z and
+    |0...0>; all-to-all jobs are the Heisenberg circuit with per-gate
+    depolarising damping p = 0.01, (1/n) sum Z and the Neel state, with a step
+    dt in [0.01, 0.03] from the job's first angle.  n, steps, eps and the group
+    are the job's own."""
+    out = []
+    for j in pi.serving_stream(2000, rate, seed)[:n_jobs]:
+        a = j["angles"]
+        if j["family"] == "ring":
+            wl = pi.config1_ring(n=j["n"], steps=j["steps"], theta_j=a[0], theta_x=a[1],
+                                 theta_z=a[2], eps=j["eps"], max_weight=10, symmetry=j["group"])
+        else:
+            wl = pi.config2_all_to_all(n=j["n"], dt=0.01 + 0.02 * a[0] / (np.pi / 2),
+                                       steps=j["steps"], p=0.01, eps=j["eps"], noise_mode=1,
+                                       symmetry=j["group"])
+        out.append((j["arrival"], wl))
+    return out
+
+
 def bench_serving(args):
     import torch
     import paper_2512_12094_gb300 as pp
     torch.cuda.set_device(0)
     pp.build()
     pp.load()
-    specs = serving_specs(args.serving, args.rate)
+    full = args.serving_full > 0
+    specs = serving_specs_full(args.serving_full, args.rate) if full else \
+        serving_specs(args.serving, args.rate)
     jobs = []
     for _, wl in specs:
         cfg = pp.pp_config_default(n_qubits=wl.circuit.n, symmetry=wl.symmetry, coeff_eps=wl.eps,
-                                   max_weight=wl.max_weight)
+                                   max_weight=wl.max_weight, noise_mode=wl.noise_mode,
+                                   noise_p=wl.noise_p)
         x, z, c = wl.observable.arrays()
         gx, gz, th = wl.circuit.gate_arrays(0)
+        # no reservation named: the server estimates it from the observable and
+        # grows it with the job's live-term count
         jobs.append(pp.make_job(cfg, x, z, c, pp.pack_gates(gx, gz), th, len(wl.circuit.layers),
-                                wl.state.bloch, True, 256 << 20))
+                                wl.state.bloch, True, 0))
 
-    def run(slots, paced):
-        server = pp.pp_server_create(slots, 150 << 30, 256 << 20)
+    def run(slots, paced, subset=None):
+        server = pp.pp_server_create(slots, 150 << 30, 0)
         t0 = time.perf_counter()
         ids = []
-        for (arrival, _), (job, _bufs) in zip(specs, jobs):
+        picked = range(len(jobs)) if subset is None else subset
+        for k in picked:
+            (arrival, _), (job, _bufs) = specs[k], jobs[k]
             if paced:
                 delay = t0 + arrival - time.perf_counter()
                 if delay > 0:
@@ -444,22 +484,38 @@ def bench_serving(args):
             print(f"{tag}: {len(bad)} failed jobs, statuses {hist}; first: {bad[0]['message']}",
                   file=sys.stderr, flush=True)
 
-    warm, _ = run(args.slots, False)  # warm-up (builds graphs, pools)
-    report_failures("warm-up", warm)
+    if not full:
+        warm, _ = run(args.slots, False)  # warm-up (builds graphs, pools)
+        report_failures("warm-up", warm)
     res, wall = run(args.slots, True)
     report_failures("timed", res)
     lat = np.array([r["latency_ms"] for r in res])
-    seq, seq_wall = run(1, False)  # plain per-job propagation, one after the other
-    err = max(abs(a["value"] - b["value"]) for a, b in zip(res, seq))
+    # the same jobs one after the other on one slot (every job for the scaled
+    # stream; for the full-size stream a sample of about 50, whose sequential
+    # time is not reported)
+    subset = None if not full else list(range(0, len(jobs), max(1, len(jobs) // 50)))
+    seq, seq_wall = run(1, False, subset)
+    pairs = zip(res if subset is None else [res[k] for k in subset], seq)
+    ok = [(a, b) for a, b in pairs if a["status"] == 0 and b["status"] == 0]
+    err = max((abs(a["value"] - b["value"]) for a, b in ok), default=None)
     line = {"metric": "served_jobs_per_s", "value": len(res) / wall, "unit": "jobs/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "serving_stream_scaled", "jobs": len(res), "rate_per_s": args.rate,
-                       "slots": args.slots, "budget_bytes": 150 << 30},
+            "config": {"workload": "serving_stream_full_sizes" if full else "serving_stream_scaled",
+                       "jobs": len(res), "rate_per_s": args.rate,
+                       "slots": args.slots, "budget_bytes": 150 << 30,
+                       "reservations": "estimated from each observable, grown with its live terms"},
+            "families": {f: sum(1 for _, wl in specs if (wl.noise_mode == 1) == (f == "a2a"))
+                         for f in ("ring", "a2a")},
+            "grows_total": int(sum(r["grows"] for r in res)),
+            "restarts_total": int(sum(r["restarts"] for r in res)),
+            "max_reserved_gb": max(r["reserved_bytes"] for r in res) / 1e9,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "run_ms": {"p50": float(np.percentile([r["run_ms"] for r in res], 50))},
             "failed": int(sum(r["status"] != 0 for r in res)),
-            "sequential_per_job": {"jobs_per_s": len(seq) / seq_wall, "wall_s": seq_wall},
+            "sequential_per_job": ({"jobs_per_s": len(seq) / seq_wall, "wall_s": seq_wall}
+                                   if subset is None else
+                                   {"jobs_checked_alone": len(seq), "wall_s": seq_wall}),
             "offered_load_wall_s": float(specs[-1][0]),
             "max_abs_diff_vs_sequential": err}
     print(json.dumps(line), flush=True)
@@ -769,8 +825,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--block-threads", type=int, default=0, choices=[0, 256, 1024],
+                    help="block size of the persistent layer kernel (0: the library default)")
     ap.add_argument("--serving", type=int, default=0,
                     help="serve N jobs of the scaled Poisson stream instead of the main job")
+    ap.add_argument("--serving-full", type=int, default=0,
+                    help="serve the first N jobs of the 2000-job stream at their stated sizes")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--workload", default="",
@@ -781,7 +841,7 @@ def main():
     args = ap.parse_args()
     if args.workload:
         bench_workload(args)
-    elif args.serving > 0:
+    elif args.serving > 0 or args.serving_full > 0:
         bench_serving(args)
     elif args.profile_layer >= 0:
         profile_layer(args)

@@ -118,11 +118,14 @@ typedef struct {
                               one kernel per gate, replayed from CUDA graphs */
   int merge_method;        /* pp_merge_method of the symmetry and identical-string merges
                               after ingest (ingest itself uses the hash table) */
-  int wait_limit;          /* polls a bounded device wait (the grid barrier between gates,
-                              a merge waiting for a claimed index slot) may take before it
-                              gives up: the kernel records the failure and returns, and the
-                              call reports PP_ERR_TIMEOUT; 0 = the default, 2^22 polls
-                              (about a second).  >= 0. */
+  int block_threads;       /* threads per block of the persistent layer kernel: 256 (several
+                              blocks per SM) or 1024 (one per SM; one-word and two-word
+                              strings, single column); 0 = 256 */
+  int wait_limit;          /* microseconds a bounded device wait (the grid barrier between
+                              gates, a merge waiting for a claimed index slot) may last before
+                              it gives up: the kernel records the failure and returns, and the
+                              call reports PP_ERR_TIMEOUT; 0 = the default, 30 s (a gate over
+                              gigabytes of batched rows takes seconds).  >= 0. */
 } pp_config;
 
 typedef struct pp_ctx pp_ctx;
@@ -147,6 +150,10 @@ typedef struct {
                               anticommute with (nor, with per-gate noise, overlap): the layer
                               kernel tests them against the OR of all keys and skips the scan */
   int64_t gates_skipped;   /* number of such gates */
+  double index_factor;     /* hash index slots per table entry of capacity (pp_tune) */
+  int64_t persistent;      /* 1: layers run in one persistent kernel, 0: one kernel per gate */
+  int64_t block_threads;   /* threads per block of the kernels that apply gates */
+  int64_t stalls;          /* times a layer stopped part way for room, grew the table and went on */
 } pp_stats_t;
 
 /* Fill *cfg with defaults: n_qubits = 0 (must be set), no symmetry, batch 1,
@@ -186,14 +193,19 @@ pp_status pp_destroy(pp_ctx* ctx);
 
 /* Autotuning (an implementation facility; the paper has no counterpart).
  * Times one application of the layer (gates in time order, theta [n_gates][batch],
- * as for pp_apply_layer, without the boundary merge) on a copy of the context's
- * current table for each candidate launch size -- 0.5, 1, 2 and 4 times the
- * default number of blocks per gate pass -- puts the table and the statistics
- * back after each trial, and keeps the fastest size for the context's later
- * layers (pp_stats_t.grid_scale; *chosen_scale when not NULL).  The terms
- * and coefficients that later calls produce do not depend on the choice; the
- * order of table entries may (merge sums use FP64 atomics, whose rounding
- * order is never fixed).  An empty table leaves the setting as it is.
+ * as for pp_apply_layer, without the boundary merge) on the context's current
+ * table and undoes it, for each candidate setting, then keeps the fastest for the
+ * context's later layers.  The search is coordinate-wise: first the launch shape
+ * (all gates of a layer in one persistent kernel where the device allows it, with
+ * blocks of 256 or 1024 threads, or one kernel per gate from CUDA graphs) together
+ * with the hash index's load factor
+ * (1.5 or 3 index slots per table entry of capacity), then the grid size (0.5, 1, 2
+ * or 4 times the default number of blocks).  A candidate whose index would not fit
+ * the memory budget is left out.  The choice is visible in pp_stats_t (grid_scale,
+ * index_factor, persistent, block_threads; *chosen_scale when not NULL).  The terms and
+ * coefficients that later calls produce do not depend on the choice; the order of
+ * table entries may (merge sums use FP64 atomics, whose rounding order is never
+ * fixed).  An empty table leaves the setting as it is.
  * Errors: as pp_apply_layer (the table is restored). */
 pp_status pp_tune(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const double* theta,
                   double* chosen_scale);
@@ -418,7 +430,9 @@ pp_status pp_server_destroy(pp_server* server);
  *    with a message beyond that);
  *  - the first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    before any stream capture.  The address belongs to the device's context
+ *    as it was then: no call may follow a cudaDeviceReset of that device in
+ *    the same process;
  *  - all calls on a device share the array: calls whose work overlaps on
  *    the device race and must be serialised by the caller.  Each call clears
  *    what it uses before using it.

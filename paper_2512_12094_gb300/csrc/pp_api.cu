@@ -114,6 +114,8 @@ struct pp_ctx {
   int sms = 1;
   int gate_bps = 4;   // resident gate-kernel blocks per SM
   int layer_bps = 0;  // co-resident layer-kernel blocks per SM (0: no cooperative path)
+  int layer_threads = kBlock;   // block size of the persistent layer kernel
+  int bps_by_threads[2] = {0, 0};  // co-resident blocks per SM with 256 / 1024 threads
   std::vector<ArgsEntry> arg_cache;
   cudaEvent_t ev_layer[2] = {nullptr, nullptr};
   Buf buf[2];
@@ -135,7 +137,7 @@ struct pp_ctx {
   bool merged = true;
   bool obs_invariant = false;
   size_t bytes = 0;
-  int64_t merges = 0, compactions = 0, regrows = 0;
+  int64_t merges = 0, compactions = 0, regrows = 0, stalls = 0;
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
   int overlap_grid = 0;
@@ -143,6 +145,8 @@ struct pp_ctx {
   std::vector<cudaEvent_t> ev_start, ev_end;  // per gate position (profile_kernels)
   double last_growth = 2.0;  // stored entries after / before the gates of the last layer
   double grid_scale = 1.0;   // blocks per launch relative to the default sizing (pp_tune)
+  double index_factor = 1.5; // hash index slots per table entry of capacity (pp_tune)
+  int grid_share = 1;        // a persistent layer launch takes at most 1/grid_share of the GPU
   double gate_ms = 0.0;
   int64_t gates_timed = 0;
   void* sort_scratch = nullptr;  // scratch of the sort-based merge (merge_method 1)
@@ -237,9 +241,12 @@ void dfree(pp_ctx* c, void* p, size_t bytes) {
 }
 
 // Index slots per dense entry of capacity: the index is a power of two of at
-// least 1.5x the capacity, so its load stays below 2/3 even when the table is
-// full (a gate stalls before that can happen) and is about 1/4 at a layer start.
-uint64_t index_cap_for(uint64_t cap) { return next_pow2(cap + cap / 2); }
+// least index_factor (1.5 unless pp_tune chose another) times the capacity, so
+// its load stays below 2/3 even when the table is full (a gate stalls before
+// that can happen) and is about 1/4 at a layer start.
+uint64_t index_cap_for(const pp_ctx* c, uint64_t cap) {
+  return next_pow2((uint64_t)std::ceil(c->index_factor * (double)cap));
+}
 
 void free_buf(pp_ctx* c, Buf& b) {
   dfree(c, b.keys, (size_t)b.cap * 16 * c->W);
@@ -255,7 +262,7 @@ void free_buf(pp_ctx* c, Buf& b) {
 pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
   b = Buf();
   b.cap = cap;
-  b.icap = index_cap_for(cap);
+  b.icap = index_cap_for(c, cap);
   pp_status st = dmalloc(c, (void**)&b.keys, (size_t)cap * 16 * c->W);
   if (st == PP_OK && c->batched) {
     st = dmalloc(c, (void**)&b.rows, (size_t)cap * c->B * c->esize);
@@ -322,11 +329,30 @@ pp_status read_ctl(pp_ctx* c) {
 pp_status check_device_error(pp_ctx* c) {
   unsigned e = c->h_ctl->error;
   if (!e) return PP_OK;
-  if (e & kErrTimeout)
+  if (e & kErrTimeout) {
+    const DevCtl& h = *c->h_ctl;
+    const char* what = h.to_kind == 1   ? "the grid barrier of the layer kernel"
+                       : h.to_kind == 2 ? "the grid barrier of the batched layer kernel"
+                       : h.to_kind == 3 ? "a claimed index slot"
+                                        : "a device wait";
     return fail(PP_ERR_TIMEOUT,
-                "a bounded device wait (grid barrier or claimed index slot) ran out");
-  if (e & kErrAppend) return fail(PP_ERR_INTERNAL, "append past table capacity");
-  return fail(PP_ERR_INTERNAL, "hash index probe bound exhausted");
+                std::string("a bounded device wait ran out: ") + what + " (gate " +
+                    std::to_string(h.to_gate) + ", counter " + std::to_string(h.to_seen) +
+                    " of " + std::to_string(h.to_target) + ")");
+  }
+  const DevCtl& h = *c->h_ctl;
+  if (e & kErrAppend) {
+    std::string where;
+    if (h.to_kind == 4)
+      where = " (gate " + std::to_string(h.to_gate) + ", position " + std::to_string(h.to_seen) +
+              " of capacity " + std::to_string(h.to_target) + ")";
+    return fail(PP_ERR_INTERNAL, "append past table capacity" + where);
+  }
+  std::string where;
+  if (h.to_kind == 5)
+    where = " (gate " + std::to_string(h.to_gate) + ", T0 " + std::to_string(h.to_seen) +
+            ", index mask " + std::to_string(h.to_target) + ")";
+  return fail(PP_ERR_INTERNAL, "hash index probe bound exhausted" + where);
 }
 
 int grid_for(pp_ctx* c, uint64_t items, int per_thread) {
@@ -384,7 +410,7 @@ pp_status ensure_capacity(pp_ctx* c, uint64_t need) {
   if (need <= c->buf[c->active].cap) return PP_OK;
   uint64_t cap = std::max<uint64_t>(need, 1024);
   cap = (cap + 1023) & ~1023ull;
-  size_t add = 2 * table_bytes(cap, index_cap_for(cap), c->W, c->row_bytes());
+  size_t add = 2 * table_bytes(cap, index_cap_for(c, cap), c->W, c->row_bytes());
   size_t keep = c->bytes - 2 * table_bytes(c->buf[0].cap, c->buf[0].icap, c->W, c->row_bytes());
   if (c->cfg.mem_budget_bytes && keep + add > c->cfg.mem_budget_bytes)
     return fail(PP_ERR_CAPACITY, "term table of capacity " + std::to_string(cap) +
@@ -675,6 +701,8 @@ pp_status validate_config(const pp_config* cfg) {
   if (cfg->merge_method != PP_MERGE_HASH && cfg->merge_method != PP_MERGE_SORT)
     return fail(PP_ERR_ARG, "unknown merge_method");
   if (cfg->wait_limit < 0) return fail(PP_ERR_ARG, "wait_limit must be >= 0");
+  if (cfg->block_threads != 0 && cfg->block_threads != 256 && cfg->block_threads != 1024)
+    return fail(PP_ERR_ARG, "block_threads must be 0, 256 or 1024");
   return PP_OK;
 }
 
@@ -827,7 +855,18 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
     int dev = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    c->layer_bps = coop ? layer_blocks_per_sm(c->W) : 0;
+    if (coop && c->batched) {
+      c->layer_bps = layer_batched_blocks_per_sm(c->W, c->f32);
+    } else if (coop) {
+      c->bps_by_threads[0] = layer_blocks_per_sm(c->W, kBlock);
+      c->bps_by_threads[1] = c->W <= 2 ? layer_blocks_per_sm(c->W, 1024) : 0;
+      // 256 threads by default: 1024-thread blocks (one per SM, a quarter of
+      // the barrier arrivals and birth reservations) measured slower on the
+      // ring job; pp_tune may still choose them
+      const int want = cfg->block_threads ? cfg->block_threads : kBlock;
+      c->layer_threads = (want == 1024 && c->bps_by_threads[1] > 0) ? 1024 : kBlock;
+      c->layer_bps = c->bps_by_threads[c->layer_threads == 1024 ? 1 : 0];
+    }
     if (cudaEventCreate(&c->ev_layer[0]) != cudaSuccess ||
         cudaEventCreate(&c->ev_layer[1]) != cudaSuccess)
       return cleanup(fail(PP_ERR_CUDA, "event creation failed"));
@@ -869,7 +908,7 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   }
   uint64_t cap = std::max<uint64_t>(4 * (uint64_t)n_terms, 1024);
   cap = (cap + 1023) & ~1023ull;
-  size_t need = 2 * table_bytes(cap, index_cap_for(cap), W, c->row_bytes()) + c->bytes;
+  size_t need = 2 * table_bytes(cap, index_cap_for(c, cap), W, c->row_bytes()) + c->bytes;
   if (cfg->mem_budget_bytes && need > cfg->mem_budget_bytes)
     return cleanup(fail(PP_ERR_CAPACITY, "initial table exceeds the memory budget"));
   if ((st = alloc_buf(c, c->buf[0], cap)) != PP_OK || (st = alloc_buf(c, c->buf[1], cap)) != PP_OK)
@@ -1193,18 +1232,20 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   PP_TRY(make_room(c, factor));
   const uint64_t n_start = std::max<uint64_t>(c->n_terms, 1);
   const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
-  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0 && !c->batched;
+  const bool layered = c->cfg.layer_kernel && c->layer_bps > 0;
   if (c->batched && !args.empty()) PP_TRY(batched_columns(c, args, src_t, theta));
   int grid_b = 1;
+  // batched rows take a warp B/32 steps per pair, so they get B/32 times the blocks
+  const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
   if (layered) {
     // persistent: one string per thread per pass, never more blocks than can
     // be co-resident (the grid barrier needs all of them)
-    const uint64_t want = (uint64_t)std::ceil((double)est * c->grid_scale / kBlock);
-    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)c->sms * c->layer_bps);
+    const int nt = c->batched ? kBlock : c->layer_threads;
+    const uint64_t want = (uint64_t)std::ceil((double)(est * rowf) * c->grid_scale / nt);
+    const uint64_t room = std::max<uint64_t>(1, (uint64_t)c->sms * c->layer_bps / c->grid_share);
+    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), room);
   } else {
-    // a power of two so that captured graphs are reused; batched rows take
-    // a warp B/32 steps per pair, so they get B/32 times the blocks
-    const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
+    // a power of two so that captured graphs are reused
     while ((double)grid_b * kBlock < (double)(est * rowf) * c->grid_scale) grid_b <<= 1;
     grid_b = std::min(grid_b, c->sms * (c->batched ? 8 : c->gate_bps));
   }
@@ -1220,8 +1261,12 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       PP_CUDA(launch_chain_init(c->stream, c->d_ctl, first));
       if (layered) {
         if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[0], c->stream));
-        PP_CUDA(launch_layer(c->W, grid_b, c->stream, c->d_desc + 2, c->d_ctl, d_args,
-                             (unsigned)args.size()));
+        if (c->batched)
+          PP_CUDA(launch_layer_batched(c->W, c->f32, grid_b, c->stream, c->d_desc + 2, c->d_ctl,
+                                       d_args, (unsigned)args.size()));
+        else
+          PP_CUDA(launch_layer(c->W, c->layer_threads, grid_b, c->stream, c->d_desc + 2, c->d_ctl,
+                               d_args, (unsigned)args.size()));
         if (c->cfg.profile_kernels) PP_CUDA(cudaEventRecord(c->ev_layer[1], c->stream));
         c->launches += 1;
       } else {
@@ -1244,9 +1289,8 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
         PP_TRY(collect_gate_times(c, first, end));
       }
       if (!c->h_ctl->stall) {
-        // stored entries after the last gate: its slot (a merge leaves the slots)
-        const int q = (int)((args.size() + 2u) % 3u);
-        const uint64_t after = c->h_ctl->base[q] + c->h_ctl->cnt[q];
+        // stored entries after the last gate (a queued merge leaves after_terms)
+        const uint64_t after = c->h_ctl->after_terms;
         c->last_growth = (double)after / (double)n_start;
         if (queue_it) {
           PP_TRY(finish_queued_merge(c));
@@ -1259,6 +1303,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       }
       // gate `end` found too little room (the queued merge did nothing):
       // compact and grow, then resume there
+      c->stalls++;
       c->n_terms = c->h_ctl->n_terms;
       c->n_live = c->h_ctl->n_live;
       PP_TRY(make_room(c, std::max<uint64_t>(factor, 4)));
@@ -1293,6 +1338,7 @@ pp_status pp_config_default(pp_config* cfg) {
   cfg->layer_kernel = 1;
   cfg->merge_method = PP_MERGE_HASH;
   cfg->wait_limit = 0;
+  cfg->block_threads = 0;
   return PP_OK;
 }
 
@@ -1420,6 +1466,45 @@ pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const do
   return st;
 }
 
+// Give both tables an index of f slots per entry of capacity (empty: the
+// caller rebuilds the active one, e.g. with restore_snapshot).  False when the
+// new index would not fit the memory budget or cannot be allocated.
+bool set_index_factor(pp_ctx* c, double f) {
+  if (f == c->index_factor) return true;
+  const double old = c->index_factor;
+  c->index_factor = f;
+  size_t grow = 0;
+  for (int b = 0; b < 2; ++b) {
+    const uint64_t icap = index_cap_for(c, c->buf[b].cap);
+    if (icap > c->buf[b].icap) grow += (size_t)(icap - c->buf[b].icap) * 8;
+  }
+  if (c->cfg.mem_budget_bytes && c->bytes + grow > c->cfg.mem_budget_bytes) {
+    c->index_factor = old;
+    return false;
+  }
+  for (int b = 0; b < 2; ++b) {
+    Buf& d = c->buf[b];
+    dfree(c, d.index, (size_t)d.icap * 8);
+    d.index = nullptr;
+    d.icap = index_cap_for(c, d.cap);
+    if (dmalloc(c, (void**)&d.index, (size_t)d.icap * 8) != PP_OK ||
+        cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream) != cudaSuccess) {
+      // fall back to the old factor (the pool just received those bytes)
+      c->index_factor = old;
+      for (int k = 0; k <= b; ++k) {
+        Buf& r = c->buf[k];
+        dfree(c, r.index, (size_t)r.icap * 8);
+        r.icap = index_cap_for(c, r.cap);
+        if (dmalloc(c, (void**)&r.index, (size_t)r.icap * 8) != PP_OK) r.index = nullptr;
+        else cudaMemsetAsync(r.index, 0, (size_t)r.icap * 8, c->stream);
+      }
+      publish_desc(c);
+      return false;
+    }
+  }
+  return publish_desc(c) == PP_OK;
+}
+
 pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
                   double* chosen_scale) {
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
@@ -1454,7 +1539,7 @@ pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* t
   static_assert(offsetof(DevCtl, gates_skipped) - offsetof(DevCtl, updates) == 32,
                 "statistics counters are contiguous");
   const int64_t launches = c->launches, merges = c->merges, compactions = c->compactions,
-                regrows = c->regrows, timed = c->gates_timed;
+                regrows = c->regrows, stalls = c->stalls, timed = c->gates_timed;
   const double gate_ms = c->gate_ms, growth = c->last_growth;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto finish = [&](pp_status st) {
@@ -1465,36 +1550,103 @@ pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* t
   };
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return finish(fail(PP_ERR_CUDA, "event creation failed"));
-  const double candidates[] = {0.5, 1.0, 2.0, 4.0};
-  double best_scale = c->grid_scale, best_ms = 1e300;
-  for (double scale : candidates) {
-    c->grid_scale = scale;
-    if (cudaEventRecord(e0, c->stream) != cudaSuccess)
-      return finish(fail(PP_ERR_CUDA, "event record failed"));
-    pp_status st = apply_layer_core(c, args, src_t, theta, 0);
+  // Coordinate search: first the launch shape (the persistent layer kernel,
+  // where the device has one, or one kernel per gate) with the hash index's
+  // load factor, at the current grid scale; then the grid scale for the
+  // winner.  Every trial applies the layer to the same table and is undone.
+  struct Trial {
+    double scale, factor;
+    int persistent;
+    int threads;  // block size of the persistent kernel
+  };
+  std::vector<Trial> trials;
+  const int lk0 = c->cfg.layer_kernel ? 1 : 0;
+  for (double f : {1.5, 3.0}) {
+    if (c->batched) {
+      if (c->layer_bps > 0) trials.push_back({c->grid_scale, f, 1, kBlock});
+    } else {
+      for (int k = 0; k < 2; ++k)
+        if (c->bps_by_threads[k] > 0) trials.push_back({c->grid_scale, f, 1, k ? 1024 : kBlock});
+    }
+    trials.push_back({c->grid_scale, f, 0, c->layer_threads});
+  }
+  Trial best = {c->grid_scale, c->index_factor, lk0, c->layer_threads};
+  double best_ms = 1e300;
+  auto run_trial = [&](const Trial& tr, pp_status* err) -> double {
+    *err = PP_OK;
+    if (!set_index_factor(c, tr.factor)) return 1e300;  // beyond the budget: not a candidate
+    pp_status st = restore_snapshot(c, snap, n0);  // the table and a fresh index
     if (st != PP_OK) {
-      restore_snapshot(c, snap, n0);
-      c->grid_scale = best_ms < 1e300 ? best_scale : 1.0;
+      *err = st;
+      return 1e300;
+    }
+    c->cfg.layer_kernel = tr.persistent;
+    c->grid_scale = tr.scale;
+    if (!c->batched) {
+      c->layer_threads = tr.threads;
+      c->layer_bps = c->bps_by_threads[tr.threads == 1024 ? 1 : 0];
+    }
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) {
+      *err = fail(PP_ERR_CUDA, "event record failed");
+      return 1e300;
+    }
+    st = apply_layer_core(c, args, src_t, theta, 0);
+    float ms = 0.f;
+    if (st == PP_OK &&
+        (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = fail(PP_ERR_CUDA, "timing a trial failed");
+    *err = st;
+    return st == PP_OK ? (double)ms : 1e300;
+  };
+  auto put_back = [&](const Trial& tr) {
+    set_index_factor(c, tr.factor);
+    c->cfg.layer_kernel = tr.persistent;
+    c->grid_scale = tr.scale;
+    if (!c->batched) {
+      c->layer_threads = tr.threads;
+      c->layer_bps = c->bps_by_threads[tr.threads == 1024 ? 1 : 0];
+    }
+    return restore_snapshot(c, snap, n0);
+  };
+  for (const Trial& tr : trials) {
+    pp_status st;
+    const double ms = run_trial(tr, &st);
+    if (st != PP_OK) {
+      put_back(best);
       return finish(st);
     }
-    float ms = 0.f;
-    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-      return finish(fail(PP_ERR_CUDA, "timing a trial failed"));
     if (ms < best_ms) {
       best_ms = ms;
-      best_scale = scale;
+      best = tr;
     }
-    const pp_status rs = restore_snapshot(c, snap, n0);
+  }
+  for (double scale : {0.5, 2.0, 4.0}) {
+    Trial tr = best;
+    tr.scale = scale;
+    pp_status st;
+    const double ms = run_trial(tr, &st);
+    if (st != PP_OK) {
+      put_back(best);
+      return finish(st);
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tr;
+    }
+  }
+  {
+    const pp_status rs = put_back(best);
     if (rs != PP_OK) return finish(rs);
   }
-  c->grid_scale = best_scale;
+  const double best_scale = best.scale;
   if (upload(c, &c->d_ctl->updates, &saved, sizeof(saved)) != cudaSuccess)
     return finish(fail(PP_ERR_CUDA, "restoring statistics failed"));
   c->launches = launches;
   c->merges = merges;
   c->compactions = compactions;
   c->regrows = regrows;
+  c->stalls = stalls;
   c->gates_timed = timed;
   c->gate_ms = gate_ms;
   c->last_growth = growth;
@@ -1680,6 +1832,10 @@ pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
   out->grid_scale = c->grid_scale;
   out->skipped_updates = c->h_ctl->skipped_updates;
   out->gates_skipped = (int64_t)c->h_ctl->gates_skipped;
+  out->index_factor = c->index_factor;
+  out->persistent = (c->cfg.layer_kernel && c->layer_bps > 0) ? 1 : 0;
+  out->block_threads = out->persistent ? (c->batched ? kBlock : c->layer_threads) : kBlock;
+  out->stalls = c->stalls;
   return PP_OK;
 }
 
@@ -1842,3 +1998,7 @@ pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 }  // extern "C"
 
 bool ppk::valid_group_code(int code, int n) { return valid_group(code, n); }
+
+void ppk::set_grid_share(pp_ctx* c, int parts) {
+  if (c) c->grid_share = std::max(1, parts);
+}

@@ -48,60 +48,62 @@ __device__ __forceinline__ Key<W> shfl_key(const Key<W>& k, int src) {
   return r;
 }
 
-// ------------------------------------------------------------ gate kernel
+// ------------------------------------------------------------ gate pass
 
+// One pair action of a batched gate: what a string's thread decided from the
+// keys, handed to whichever warp of the block streams the rows.
+template <int W>
+struct RowAction {
+  Key<W> R;        // the partner key (births)
+  uint32_t ii;     // the string's row
+  int32_t jj;      // the partner's row, -1 when absent
+  uint8_t act;     // 1 damp only, 2 owned pair, 3 birth of the partner, 4 rotate only
+  uint8_t kq, kr;  // non-identity letters on the gate's support (damping)
+  uint8_t flags;   // 1 string alive, 2 partner alive, 4 i P Q = -R
+};
+
+// Shared memory of one batched gate pass.
 template <int W, typename T>
-__global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __restrict__ tabp,
-                                                              DevCtl* __restrict__ ctl,
-                                                              GateArgs g) {
+struct BatchedShared {
+  long long delta[kBlock / 32];
+  unsigned long long ac[kBlock / 32];
+  unsigned wcnt[kBlock / 32];
+  unsigned err;
+  T cs[2 * 512];  // this gate's cos[0, B), sin[B, 2B) (B <= 512)
+  RowAction<W> queue[kBlock];
+};
+
+// Columns a lane streams at once: each lane holds kColU columns of each row in
+// registers, so the loads of a whole 256-column FP64 row pair are in flight
+// together instead of one column at a time.
+constexpr int kColU = 8;
+
+// One gate over the rows [0, T0) by one block.  The block takes kBlock
+// strings at a time (block-stride); every thread decides its string's action
+// from the keys, the actions are compacted into a shared queue, and the
+// block's warps take them in turn, each streaming the rows of one action with
+// coalesced loads and stores.  So a chunk with many actions keeps every warp
+// busy.  Births go to T0 + atomicAdd(cnt_slot); the block's live-count change
+// goes to *dlt_slot and its anticommuting count to ctl->ac_total.  Every
+// thread of the block must call this; it ends with the block synchronised.
+template <int W, typename T>
+__device__ __forceinline__ void gate_pass_batched(const DevTable& t, DevCtl* ctl, const GateArgs& g,
+                                                  uint64_t T0, unsigned long long* cnt_slot,
+                                                  long long* dlt_slot, BatchedShared<W, T>& sh) {
   constexpr int kWarps = kBlock / 32;
-  __shared__ long long s_delta[kWarps];
-  __shared__ unsigned long long s_ac[kWarps];
-  __shared__ unsigned s_err;
-  __shared__ T s_cs[2 * 512];  // this gate's cos[0, B), sin[B, 2B) (B <= 512)
-  const unsigned gid = g.gate_id;
-  const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const DevTable t = *tabp;
-  const unsigned long long T0 = __ldcg(&ctl->base[prev]) + __ldcg(&ctl->cnt[prev]);
-  const long long L0 = __ldcg(&ctl->live_base[prev]) + __ldcg(&ctl->dlt[prev]);
-  bool run = (gid >= __ldcg(&ctl->first_gate)) && (__ldcg(&ctl->stall) == 0u) &&
-             (__ldcg(&ctl->error) == 0u);
-  const bool room = 2ull * T0 <= t.cap;
-  if (threadIdx.x == 0) {
-    if (blockIdx.x == 0 && run && !room) ctl->stall = gid + 1;
-    if (blockIdx.x == 0 && run && room) {
-      ctl->base[slot] = T0;
-      ctl->live_base[slot] = L0;
-      ctl->cnt[next] = 0;
-      ctl->dlt[next] = 0;
-      atomicAdd(&ctl->updates, (double)L0);
-      atomicAdd(&ctl->gates_done, 1ull);
-    }
-    s_err = 0;
-  }
-  if (!(run && room)) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    return;
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = t.B;
   T* rows = static_cast<T*>(t.rows);
-  // cos and sin of every column, read by every action: staged once per block
-  for (int k = threadIdx.x; k < 2 * B; k += kBlock) s_cs[k] = static_cast<const T*>(g.csb)[k];
-  __syncthreads();
-  const T* cs = s_cs;
+  const T* cs = sh.cs;
   const bool noise = g.damp != nullptr;
   const bool use_eps = g.use_eps != 0;
   const uint64_t eb = use_eps ? eps_bits_of<T>(g.eps) : 0ull;
   long long delta = 0;
   unsigned long long n_ac = 0;
   unsigned err = 0;
-  const uint64_t wstride = (uint64_t)gridDim.x * kWarps * 32;
-  for (uint64_t base = ((uint64_t)blockIdx.x * kWarps + warp) * 32; base < T0; base += wstride) {
-    const uint64_t i = base + lane;
-    // act: 1 damp only, 2 pair owned by this string, 3 birth of the partner,
-    //      4 partner too heavy to keep (this string only rotates)
+  const uint64_t bstride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t cbase = (uint64_t)blockIdx.x * kBlock; cbase < T0; cbase += bstride) {
+    const uint64_t i = cbase + threadIdx.x;
     int act = 0, kq = 0, kr = 0;
     int64_t jr = -1;
     bool aliveQ = false, aliveR = false, neg = false;
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         if (aliveQ || pw == 0) {
           const uint64_t h = key_hash(R);
           jr = index_find_old<W>(t, R, h, tag_of(h), T0, err);
+          if (jr == -2) note_first(ctl, 5u, g.gate_id, (unsigned)T0, (unsigned)t.imask);
         }
         neg = sigma_of<W>(g, Q) < 0;
         // live anticommuting rows from values before the gate: the owner
@@ -151,51 +154,102 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         }
       }
     }
-    unsigned todo = __ballot_sync(kAll, act != 0);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int a = __shfl_sync(kAll, act, src);
-      const uint64_t ii = __shfl_sync(kAll, i, src);
-      const long long jj = __shfl_sync(kAll, (long long)jr, src);
-      const bool aQ = __shfl_sync(kAll, (int)aliveQ, src) != 0;
-      const bool aR = __shfl_sync(kAll, (int)aliveR, src) != 0;
-      const bool ng = __shfl_sync(kAll, (int)neg, src) != 0;
-      const int kqq = __shfl_sync(kAll, kq, src), krr = __shfl_sync(kAll, kr, src);
+    // compact the block's actions into the queue, in string order
+    const unsigned bal = __ballot_sync(kAll, act != 0);
+    if (lane == 0) sh.wcnt[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, n_queue = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      before += (w < warp) ? sh.wcnt[w] : 0u;
+      n_queue += sh.wcnt[w];
+    }
+    if (act) {
+      RowAction<W>& a = sh.queue[before + __popc(bal & ((1u << lane) - 1u))];
+      a.R = R;
+      a.ii = (uint32_t)i;
+      a.jj = (int32_t)jr;
+      a.act = (uint8_t)act;
+      a.kq = (uint8_t)kq;
+      a.kr = (uint8_t)kr;
+      a.flags = (uint8_t)((aliveQ ? 1 : 0) | (aliveR ? 2 : 0) | (neg ? 4 : 0));
+    }
+    __syncthreads();
+    for (unsigned q = warp; q < n_queue; q += kWarps) {
+      const RowAction<W>& A = sh.queue[q];
+      const int a = A.act;
+      const uint64_t ii = A.ii;
+      const long long jj = A.jj;
+      const bool aQ = (A.flags & 1) != 0, aR = (A.flags & 2) != 0, ng = (A.flags & 4) != 0;
+      const int kqq = A.kq, krr = A.kr;
       const T fq = kqq ? (T)g.damp[kqq] : (T)1, fr = krr ? (T)g.damp[krr] : (T)1;
       T* rq = rows + ii * B;
       bool anyQ = false, anyR = false;
       if (a == 1) {
-        #pragma unroll 4
-        for (int col = lane; col < B; col += 32) {
-          const T v = mul_rn(ld_row(rq + col), fq);
-          rq[col] = v;
-          anyQ |= big(v, eb);
+        for (int c0 = 0; c0 < B; c0 += 32 * kColU) {
+          T v[kColU];
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            v[u] = col < B ? ld_row(rq + col) : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            if (col < B) {
+              const T d = mul_rn(v[u], fq);
+              rq[col] = d;
+              anyQ |= big(d, eb);
+            }
+          }
         }
       } else if (a == 2) {
         T* rr = rows + (uint64_t)jj * B;
-        #pragma unroll 4
-        for (int col = lane; col < B; col += 32) {
-          T dq = aQ ? ld_row(rq + col) : (T)0, dr = aR ? ld_row(rr + col) : (T)0;
-          if (kqq) dq = mul_rn(dq, fq);
-          if (krr) dr = mul_rn(dr, fr);
-          const T c = cs[col], s = cs[B + col];
-          const T sQ = mul_rn(s, dq), sR = mul_rn(s, dr);
-          const T nq = add_rn(mul_rn(c, dq), flip(sR, !ng));
-          const T nr = add_rn(mul_rn(c, dr), flip(sQ, ng));
-          rq[col] = nq;
-          rr[col] = nr;
-          anyQ |= big(nq, eb);
-          anyR |= big(nr, eb);
+        for (int c0 = 0; c0 < B; c0 += 32 * kColU) {
+          T vq[kColU], vr[kColU];
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            vq[u] = (col < B && aQ) ? ld_row(rq + col) : (T)0;
+            vr[u] = (col < B && aR) ? ld_row(rr + col) : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            if (col < B) {
+              T dq = vq[u], dr = vr[u];
+              if (kqq) dq = mul_rn(dq, fq);
+              if (krr) dr = mul_rn(dr, fr);
+              const T c = cs[col], sn = cs[B + col];
+              const T sQ = mul_rn(sn, dq), sR = mul_rn(sn, dr);
+              const T nq = add_rn(mul_rn(c, dq), flip(sR, !ng));
+              const T nr = add_rn(mul_rn(c, dr), flip(sQ, ng));
+              rq[col] = nq;
+              rr[col] = nr;
+              anyQ |= big(nq, eb);
+              anyR |= big(nr, eb);
+            }
+          }
         }
       } else {
         // first pass: which of Q's new row and the child row survive
-        #pragma unroll 4
-        for (int col = lane; col < B; col += 32) {
-          T dq = ld_row(rq + col);
-          if (kqq) dq = mul_rn(dq, fq);
-          anyQ |= big(mul_rn(cs[col], dq), eb);
-          if (a == 3) anyR |= big(mul_rn(cs[B + col], dq), eb);
+        for (int c0 = 0; c0 < B; c0 += 32 * kColU) {
+          T v[kColU];
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            v[u] = col < B ? ld_row(rq + col) : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            if (col < B) {
+              T dq = v[u];
+              if (kqq) dq = mul_rn(dq, fq);
+              anyQ |= big(mul_rn(cs[col], dq), eb);
+              if (a == 3) anyR |= big(mul_rn(cs[B + col], dq), eb);
+            }
+          }
         }
       }
       anyQ = __any_sync(kAll, anyQ) || !use_eps;
@@ -204,30 +258,44 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         const bool birth = (a == 3) && anyR;
         unsigned long long idx = 0;
         if (birth) {
-          if (lane == 0) idx = T0 + atomicAdd(&ctl->cnt[slot], 1ull);
+          if (lane == 0) idx = T0 + atomicAdd(cnt_slot, 1ull);
           idx = __shfl_sync(kAll, idx, 0);
           if (idx >= t.cap) {
             err |= kErrAppend;
+            if (lane == 0) note_first(ctl, 4u, g.gate_id, (unsigned)idx, (unsigned)t.cap);
           }
         }
         const bool write_child = birth && idx < t.cap;
         T* rn = rows + idx * B;
-        #pragma unroll 4
-        for (int col = lane; col < B; col += 32) {
-          T dq = ld_row(rq + col);
-          if (kqq) dq = mul_rn(dq, fq);
-          rq[col] = mul_rn(cs[col], dq);
-          if (write_child) rn[col] = flip(mul_rn(cs[B + col], dq), ng);
+        for (int c0 = 0; c0 < B; c0 += 32 * kColU) {
+          T v[kColU];
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            v[u] = col < B ? ld_row(rq + col) : (T)0;
+          }
+#pragma unroll
+          for (int u = 0; u < kColU; ++u) {
+            const int col = c0 + 32 * u + lane;
+            if (col < B) {
+              T dq = v[u];
+              if (kqq) dq = mul_rn(dq, fq);
+              rq[col] = mul_rn(cs[col], dq);
+              if (write_child) rn[col] = flip(mul_rn(cs[B + col], dq), ng);
+            }
+          }
         }
-        const Key<W> Rs = shfl_key<W>(R, src);
         if (lane == 0) {
           t.alive[ii] = anyQ ? 1 : 0;
           delta += (long long)anyQ - 1;
           if (write_child) {
+            const Key<W> Rs = A.R;
             st_key<W>(t.keys, idx, Rs);
             t.alive[idx] = 1;
             const uint64_t h = key_hash(Rs);
+            const unsigned e0 = err;
             index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+            if (err != e0) note_first(ctl, 5u, g.gate_id, (unsigned)T0, (unsigned)t.imask);
             delta += 1;
           }
         }
@@ -242,26 +310,211 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
         }
       }
     }
+    __syncthreads();  // the queue is rewritten by the next chunk
   }
-  asm volatile("griddepcontrol.launch_dependents;");
   delta = warp_sum(delta);
   n_ac = warp_sum(n_ac);
   if (lane == 0) {
-    s_delta[warp] = delta;
-    s_ac[warp] = n_ac;
+    sh.delta[warp] = delta;
+    sh.ac[warp] = n_ac;
   }
-  if (err) atomicOr(&s_err, err);
+  if (err) atomicOr(&sh.err, err);
   __syncthreads();
   if (threadIdx.x == 0) {
     long long d = 0;
     unsigned long long ac = 0;
     for (int w = 0; w < kWarps; ++w) {
-      d += s_delta[w];
-      ac += s_ac[w];
+      d += sh.delta[w];
+      ac += sh.ac[w];
     }
-    if (d) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->dlt[slot]), (unsigned long long)d);
+    if (d) atomicAdd(reinterpret_cast<unsigned long long*>(dlt_slot), (unsigned long long)d);
     if (ac) atomicAdd(&ctl->ac_total, ac);
-    if (s_err) atomicOr(&ctl->error, s_err);
+    if (sh.err) {
+      atomicOr(&ctl->error, sh.err);
+      atomicOr(&ctl->gerr[cnt_slot - ctl->cnt], sh.err);
+    }
+    sh.err = 0;
+  }
+  __syncthreads();
+}
+
+template <int W, typename T>
+__device__ __forceinline__ void stage_columns(BatchedShared<W, T>& sh, const GateArgs& g, int B) {
+  for (int k = threadIdx.x; k < 2 * B; k += kBlock) sh.cs[k] = static_cast<const T*>(g.csb)[k];
+}
+
+// One kernel per gate (the graph / PDL path), with the slot protocol of the
+// single-column gate_kernel.
+template <int W, typename T>
+__global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __restrict__ tabp,
+                                                              DevCtl* __restrict__ ctl,
+                                                              GateArgs g) {
+  __shared__ BatchedShared<W, T> sh;
+  const unsigned gid = g.gate_id;
+  const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const DevTable t = *tabp;
+  const unsigned long long T0 = __ldcg(&ctl->base[prev]) + __ldcg(&ctl->cnt[prev]);
+  const long long L0 = __ldcg(&ctl->live_base[prev]) + __ldcg(&ctl->dlt[prev]);
+  bool run = (gid >= __ldcg(&ctl->first_gate)) && (__ldcg(&ctl->stall) == 0u) &&
+             (__ldcg(&ctl->error) == 0u);
+  const bool room = 2ull * T0 <= t.cap;
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && run && !room) ctl->stall = gid + 1;
+    if (blockIdx.x == 0 && run && room) {
+      ctl->base[slot] = T0;
+      ctl->live_base[slot] = L0;
+      ctl->cnt[next] = 0;
+      ctl->dlt[next] = 0;
+      ctl->gerr[next] = 0;
+      atomicAdd(&ctl->updates, (double)L0);
+      atomicAdd(&ctl->gates_done, 1ull);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        if (g.px[j]) atomicOr(&ctl->occ[j], (unsigned long long)g.px[j]);
+        if (g.pz[j]) atomicOr(&ctl->occ[kMaxW + j], (unsigned long long)g.pz[j]);
+      }
+    }
+    sh.err = 0;
+  }
+  if (!(run && room)) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    return;
+  }
+  stage_columns<W, T>(sh, g, t.B);
+  __syncthreads();
+  gate_pass_batched<W, T>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], sh);
+  asm volatile("griddepcontrol.launch_dependents;");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32b(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of the cooperative batched layer kernel (the same protocol as
+// the single-column layer kernel: a counter that only grows, release /
+// acquire, bounded wait).
+__device__ __forceinline__ bool grid_sync_b(DevCtl* ctl, unsigned& target, int& s_ok,
+                                            unsigned limit, unsigned gate) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->bar_root), "r"(1u)
+                 : "memory");
+    const unsigned long long deadline = wait_deadline(limit);
+    unsigned seen;
+    while ((int)((seen = ld_acquire_u32b(&ctl->bar_root)) - target) < 0) {
+      if (global_ns() > deadline) {
+        ok = 0;
+        note_timeout(ctl, 2u, gate, seen, target);
+        break;
+      }
+      __nanosleep(16);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// All gates of a batched layer in one cooperative launch, organised like the
+// single-column layer_kernel: the table size travels in registers, gates are
+// separated by a grid barrier, gates that no stored string can touch are
+// skipped by the occupancy test, and executed gates take the counter slots
+// by their ordinal.  On leaving, block 0 records the state in the exit
+// record, which chain_finish reads.
+template <int W, typename T>
+__global__ void __launch_bounds__(kBlock)
+    layer_batched_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
+                         const GateArgs* __restrict__ gates, unsigned n_gates) {
+  __shared__ BatchedShared<W, T> sh;
+  __shared__ GateArgs s_gate;
+  __shared__ int s_ok;
+  const DevTable t = *tabp;
+  const unsigned first = __ldcg(&ctl->first_gate);
+  const int q0 = (int)((first + 2u) % 3u);
+  unsigned long long T0 = __ldcg(&ctl->base[q0]) + __ldcg(&ctl->cnt[q0]);
+  long long L0 = __ldcg(&ctl->live_base[q0]) + __ldcg(&ctl->dlt[q0]);
+  uint64_t ox[W], oz[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ox[j] = __ldcg(&ctl->occ[j]);
+    oz[j] = __ldcg(&ctl->occ[kMaxW + j]);
+  }
+  unsigned target = 0;
+  const unsigned wlimit = wait_limit_of(ctl);
+  if (threadIdx.x == 0) sh.err = 0;
+  if (__ldcg(&ctl->entry_stop) != 0u) return;  // written before the launch: uniform
+  unsigned e = 0;
+  unsigned end = n_gates;
+  for (unsigned gid = first; gid < n_gates; ++gid) {
+    __syncthreads();  // the previous gate's readers of s_gate and sh.cs are done
+    {
+      const unsigned* src = reinterpret_cast<const unsigned*>(gates + gid);
+      unsigned* dst = reinterpret_cast<unsigned*>(&s_gate);
+      for (unsigned k = threadIdx.x; k < sizeof(GateArgs) / 4; k += kBlock) dst[k] = __ldg(src + k);
+    }
+    __syncthreads();
+    const GateArgs& g = s_gate;
+    uint64_t touch = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      touch |= (g.px[j] & oz[j]) | (g.pz[j] & ox[j]);
+      if (g.damp) touch |= g.supp[j] & (ox[j] | oz[j]);
+    }
+    if (touch == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(&ctl->updates, (double)L0);
+        atomicAdd(&ctl->gates_done, 1ull);
+        atomicAdd(&ctl->skipped_updates, (double)L0);
+        atomicAdd(&ctl->gates_skipped, 1ull);
+      }
+      continue;
+    }
+    if (2ull * T0 > t.cap) {  // the same decision in every block
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->stall = gid + 1;
+      end = gid;
+      break;
+    }
+    const int slot = (int)(e % 3u), next = (int)((e + 1u) % 3u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->cnt[next] = 0;
+      ctl->dlt[next] = 0;
+      ctl->gerr[next] = 0;
+      atomicAdd(&ctl->updates, (double)L0);
+      atomicAdd(&ctl->gates_done, 1ull);
+    }
+    stage_columns<W, T>(sh, g, t.B);
+    __syncthreads();
+    gate_pass_batched<W, T>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], sh);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      ox[j] |= g.px[j];
+      oz[j] |= g.pz[j];
+    }
+    if (gridDim.x == 1) {
+      __threadfence();
+      __syncthreads();
+    } else if (!grid_sync_b(ctl, target, s_ok, wlimit, gid)) {
+      return;
+    }
+    T0 += __ldcg(&ctl->cnt[slot]);
+    L0 += __ldcg(&ctl->dlt[slot]);
+    ++e;
+    if (__ldcg(&ctl->gerr[slot]) != 0u) return;  // written by this gate only: uniform
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->exit_terms = T0;
+    ctl->exit_live = L0;
+    ctl->exit_set = 1u;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      ctl->occ[j] = ox[j];
+      ctl->occ[kMaxW + j] = oz[j];
+    }
   }
 }
 
@@ -280,6 +533,7 @@ __global__ void __launch_bounds__(kBlock)
   const int B = dst.B;
   const unsigned wlimit = wait_limit_of(ctl);
   unsigned err = 0;
+  OccAcc<W> occ;
   unsigned long long* index = reinterpret_cast<unsigned long long*>(dst.index);
   const uint64_t wstride = (uint64_t)gridDim.x * kWarps;
   for (uint64_t e = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); e < count; e += wstride) {
@@ -288,6 +542,7 @@ __global__ void __launch_bounds__(kBlock)
       Key<W> K = ld_key<W>(src_keys, e);
       if (wmax < 0 || weight(K) <= wmax) {
         canon<W, G>(K, n, lx);
+        occ.add(K);
         const uint64_t h = key_hash(K);
         const uint32_t tag = tag_of(h);
         uint64_t pos = h & dst.imask;
@@ -311,14 +566,17 @@ __global__ void __launch_bounds__(kBlock)
             sv = old;
           }
           if ((uint32_t)(sv >> 32) == tag) {
-            unsigned spins = 0;
-            while ((uint32_t)sv == kPendingIdx && spins < wlimit) {
-              ++spins;
-              __nanosleep(64);
-              sv = *reinterpret_cast<volatile unsigned long long*>(index + pos);
+            // read the slot again with acquire semantics before using its position
+            sv = ld_acquire_u64(index + pos);
+            if ((uint32_t)sv == kPendingIdx) {
+              const unsigned long long deadline = wait_deadline(wlimit);
+              while ((uint32_t)sv == kPendingIdx && global_ns() <= deadline) {
+                __nanosleep(64);
+                sv = ld_acquire_u64(index + pos);
+              }
             }
             if ((uint32_t)sv == kPendingIdx) {
-              err |= kErrTimeout;
+              note_timeout(ctl, 3u, 0u, (unsigned)pos, 0u);
               break;
             }
             if (keys_equal(ld_key_cg<W>(dst.keys, (uint32_t)sv), K)) {
@@ -337,6 +595,7 @@ __global__ void __launch_bounds__(kBlock)
       for (int col = lane; col < B; col += 32) atomicAdd(ar + col, (double)sr[col]);
     }
   }
+  occ.flush(ctl);
   if (err) atomicOr(&ctl->error, err);
 }
 
@@ -383,6 +642,7 @@ __global__ void __launch_bounds__(kBlock)
   const uint64_t xb = extra_eps > 0.0 ? eps_bits_of<T>(extra_eps) : 0ull;
   unsigned err = 0;
   long long live = 0;
+  OccAcc<W> occ;
   const uint64_t wstride = (uint64_t)gridDim.x * kWarps * 32;
   for (uint64_t base = ((uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * 32; base < count;
        base += wstride) {
@@ -422,6 +682,7 @@ __global__ void __launch_bounds__(kBlock)
       if (lane == 0) {
         const Key<W> K = ld_key<W>(src.keys, e);
         st_key<W>(dst.keys, k, K);
+        occ.add(K);
         dst.alive[k] = 1;
         ++live;
         if (with_index) {
@@ -433,6 +694,7 @@ __global__ void __launch_bounds__(kBlock)
   }
   if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live),
                                    (unsigned long long)live);
+  occ.flush(ctl);
   if (err) atomicOr(&ctl->error, err);
 }
 
@@ -511,6 +773,49 @@ static cudaError_t launch_gate_batched_w(int grid, cudaStream_t s, const DevTabl
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, gate_batched_kernel<W, T>, tab, ctl, g);
+}
+
+template <int W, typename T>
+static cudaError_t launch_layer_batched_w(int grid, cudaStream_t s, const DevTable* tab,
+                                          DevCtl* ctl, const GateArgs* gates, unsigned n_gates) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, layer_batched_kernel<W, T>, tab, ctl, gates, n_gates);
+}
+
+cudaError_t launch_layer_batched(int W, int f32, int grid, cudaStream_t s, const DevTable* tab,
+                                 DevCtl* ctl, const GateArgs* gates, unsigned n_gates) {
+  if (f32) {
+    PPB_W(W, return (launch_layer_batched_w<WW, float>(grid, s, tab, ctl, gates, n_gates)));
+  } else {
+    PPB_W(W, return (launch_layer_batched_w<WW, double>(grid, s, tab, ctl, gates, n_gates)));
+  }
+  return cudaErrorInvalidValue;
+}
+
+int layer_batched_blocks_per_sm(int W, int f32) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define PPB_OCC(WW)                                                                         \
+  e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_batched_kernel<WW, float>, \
+                                                          kBlock, 0)                          \
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_batched_kernel<WW, double>, \
+                                                          kBlock, 0)
+  switch (W) {
+    case 1: PPB_OCC(1); break;
+    case 2: PPB_OCC(2); break;
+    case 3: PPB_OCC(3); break;
+    case 4: PPB_OCC(4); break;
+  }
+#undef PPB_OCC
+  return (e == cudaSuccess && nb > 0) ? nb : 0;
 }
 
 cudaError_t launch_gate_batched(int W, int f32, int grid, cudaStream_t s, const DevTable* tab,

@@ -10,11 +10,41 @@ namespace {
 
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-// Default bound of a device wait (a grid barrier or a pending index slot):
-// 2^22 polls with a short sleep, well under a second on this GPU.  A context
-// may set another bound (DevCtl::wait_limit); a wait that runs out sets
-// kErrTimeout and returns, so the host reports PP_ERR_TIMEOUT.
-constexpr unsigned kDefaultWaitLimit = 1u << 22;
+// Default bound of a device wait (a grid barrier or a pending index slot),
+// in microseconds of the GPU's global timer: 30 s, far above the longest
+// gate (a gate over gigabytes of batched rows takes seconds) and far below a
+// hang.  A context may set another bound (DevCtl::wait_limit); a wait that
+// runs out sets kErrTimeout and returns, so the host reports PP_ERR_TIMEOUT.
+constexpr unsigned kDefaultWaitLimit = 30u * 1000u * 1000u;
+
+// Record the first device error with where it happened (only the first
+// record is kept); the caller sets the error bit.
+__device__ __forceinline__ void note_first(DevCtl* ctl, unsigned kind, unsigned gate,
+                                           unsigned a, unsigned b) {
+  if (atomicCAS(&ctl->to_kind, 0u, kind) == 0u) {
+    ctl->to_gate = gate;
+    ctl->to_seen = a;
+    ctl->to_target = b;
+  }
+}
+
+// Record where a bounded wait gave up and set the timeout error bit.
+__device__ __forceinline__ void note_timeout(DevCtl* ctl, unsigned kind, unsigned gate,
+                                             unsigned seen, unsigned target) {
+  note_first(ctl, kind, gate, seen, target);
+  atomicOr(&ctl->error, kErrTimeout);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Deadline of a wait that starts now, limit_us microseconds away.
+__device__ __forceinline__ unsigned long long wait_deadline(unsigned limit_us) {
+  return global_ns() + 1000ull * (unsigned long long)limit_us;
+}
 // A merge queued behind a layer before the layer's outcome is known does
 // nothing when a gate of that layer stopped for capacity or failed.
 __device__ __forceinline__ bool queued_layer_stopped(const DevCtl* ctl) {
@@ -173,6 +203,29 @@ struct OccAcc {
     }
   }
 };
+
+// Acquire load of an index slot: pairs with the fence and exchange that
+// publish a slot's dense position, so the key and coefficient written before
+// the publication are visible to the reader.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Claim an empty slot with a pending position (published later by its
+// owner); returns the slot, or ~0 (error bit set) if the probe bound runs out.
+__device__ __forceinline__ uint64_t index_claim_pending(const DevTable& t, uint64_t pos,
+                                                        uint32_t tag, unsigned& err) {
+  unsigned long long* idx = reinterpret_cast<unsigned long long*>(t.index);
+  const unsigned long long val = ((unsigned long long)tag << 32) | kPendingIdx;
+  for (uint64_t probe = 0; probe <= t.imask; ++probe) {
+    if (atomicCAS(idx + pos, 0ull, val) == 0ull) return pos;
+    pos = (pos + 1) & t.imask;
+  }
+  err |= kErrProbe;
+  return ~0ull;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

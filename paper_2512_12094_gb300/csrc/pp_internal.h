@@ -57,11 +57,17 @@ struct alignas(128) DevCtl {
   unsigned int stall;          // 1 + id of a gate that found too little capacity; 0 = none
   unsigned int first_gate;     // gates with a smaller layer-local id skip themselves
   unsigned int error;          // error bits (any kernel)
-  unsigned int wait_limit;     // iterations a bounded device wait may spin; 0 = the default
+  unsigned int wait_limit;     // microseconds a bounded device wait may last; 0 = the default
   alignas(128) unsigned long long base[3];  // stored entries entering the gate of a slot
   long long live_base[3];                   // live entries entering the gate of a slot
   alignas(128) unsigned long long cnt[3];   // births appended by the gate of a slot
   alignas(128) long long dlt[3];            // live-count change by the gate of a slot
+  // error bits raised by the gate of a slot (also ORed into error).  A
+  // cooperative layer reads the slot of the gate it has just finished after
+  // the grid barrier: only that gate's blocks can have written it, so every
+  // block takes the same decision, whereas error may already hold a bit set
+  // by a fast block in the next gate.
+  unsigned int gerr[3];
   alignas(128) double updates;              // sum of live terms entering each gate
   unsigned long long gates_done;
   unsigned long long ac_total;              // sum of live anticommuting terms per gate
@@ -71,9 +77,30 @@ struct alignas(128) DevCtl {
   // is allowed): a gate P with (x_P & occ_z) | (z_P & occ_x) == 0 commutes
   // with every string, so the layer kernel skips it without a scan.
   alignas(128) unsigned long long occ[2 * kMaxW];
+  // State a cooperative layer kernel leaves on exit (block 0 writes it): the
+  // stored and live entries after the last gate it applied.  It has lines of
+  // its own because other blocks may still be reading the gate slots when
+  // block 0 leaves.  chain_finish takes it when exit_set is 1, else the slot
+  // of the last gate; it copies the stored count to after_terms, which a
+  // merge queued behind the layer leaves alone.
+  alignas(128) unsigned long long exit_terms;
+  long long exit_live;
+  unsigned int exit_set;
+  unsigned int entry_stop;  // chain_init: an error was already set (every block returns)
+  unsigned long long after_terms;
   alignas(128) unsigned long long n_next;   // append cursor of merge / compaction kernels
   alignas(128) unsigned int bar_root;       // grid-barrier counter of the cooperative layer
                                             // kernel (grows by gridDim per barrier)
+  // The first device error and where it happened: kind 1 grid barrier of
+  // the layer kernel, 2 of the batched layer kernel, 3 claimed index slot
+  // (bounded waits that ran out: the counter seen against the one waited
+  // for); 4 a birth past the capacity (its position and the capacity); 5 an
+  // index probe that walked the whole index (T0 and the index mask); with
+  // the layer-local gate id.
+  alignas(128) unsigned int to_kind;
+  unsigned int to_gate;
+  unsigned int to_seen;
+  unsigned int to_target;
 };
 
 struct GateArgs {
@@ -121,10 +148,12 @@ cudaError_t launch_ctl_commit(cudaStream_t s, DevCtl* ctl, int guarded);
 cudaError_t launch_chain_finish(cudaStream_t s, DevCtl* ctl, unsigned n_gates);
 
 // All gates of a layer in one cooperative launch (grid <= co-resident blocks);
-// gates points to n_gates GateArgs in device memory.
-cudaError_t launch_layer(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
-                         const GateArgs* gates, unsigned n_gates);
-int layer_blocks_per_sm(int W);  // co-resident layer-kernel blocks per SM (0: unknown)
+// gates points to n_gates GateArgs in device memory.  threads: block size,
+// 256 or 1024 (1024 for W <= 2 only).
+cudaError_t launch_layer(int W, int threads, int grid, cudaStream_t s, const DevTable* tab,
+                         DevCtl* ctl, const GateArgs* gates, unsigned n_gates);
+// co-resident layer-kernel blocks per SM for that block size (0: none)
+int layer_blocks_per_sm(int W, int threads);
 
 // One gate kernel.  With pdl set it is launched with programmatic stream
 // serialisation: it may start while the previous kernel on the stream
@@ -190,10 +219,23 @@ void set_last_error(const std::string& msg);
 // byte for PP_SYM_TORUS) for n qubits?
 bool valid_group_code(int code, int n);
 
+}  // namespace ppk
+struct pp_ctx;
+namespace ppk {
+// Limit a context's persistent layer launches to 1/parts of the GPU's
+// co-resident blocks, so that `parts` contexts running at once (the server's
+// jobs) can overlap.
+void set_grid_share(pp_ctx* c, int parts);
+
 // ------------------------------------------------------- batched launchers
 // Same contracts as the single-column kernels above, on B-column rows.
 cudaError_t launch_gate_batched(int W, int f32, int grid, cudaStream_t s, const DevTable* tab,
                                 DevCtl* ctl, const GateArgs& g, bool pdl);
+// All gates of a batched layer in one cooperative launch (grid <= co-resident
+// blocks), as launch_layer for the single column.
+cudaError_t launch_layer_batched(int W, int f32, int grid, cudaStream_t s, const DevTable* tab,
+                                 DevCtl* ctl, const GateArgs* gates, unsigned n_gates);
+int layer_batched_blocks_per_sm(int W, int f32);  // 0: no cooperative path
 // src rows: element type f32 (1) / double (0), or double input rows when
 // src_alive == nullptr (ingest); acc: [cap][B] doubles, zeroed by the caller.
 cudaError_t launch_merge_batched(int W, int group, int n, int wmax, int src_f32, int grid,

@@ -29,11 +29,12 @@ namespace {
 // Births (partners not yet in the table) are staged in shared memory and
 // appended with one atomic per block at the end of a gate; a block whose
 // staging area fills up appends the rest directly, one atomic per warp.
-template <int W>
+template <int W, int NT = kBlock>
 struct GateStage {
-  static constexpr int kCap = (W == 1) ? 512 : ((W <= 3) ? 256 : 128);
+  static constexpr int kCap = ((W == 1) ? 512 : ((W <= 3) ? 256 : 128)) * NT / kBlock;
   uint64_t key[kCap][2 * W];
   double coef[kCap];
+  uint64_t slot[kCap];  // index slot claimed for the birth (pending until published)
 };
 
 // Per-warp worklist.  A warp scans kU strings per lane (all loads in flight
@@ -41,17 +42,18 @@ struct GateStage {
 // here, then works through the list with every lane busy: the dependent
 // lookup chain (index slot -> partner key -> coefficients) then runs once per
 // 32 anticommuting strings instead of once per 32 scanned strings.
-template <int W>
+template <int W, int NT = kBlock>
 struct GateList {
   static constexpr int kU = (W <= 2) ? 4 : 2;
   static constexpr int kItems = 32 * kU;
-  uint64_t key[kBlock / 32][kItems][2 * W];
-  unsigned short off[kBlock / 32][kItems];
+  uint64_t key[NT / 32][kItems][2 * W];
+  unsigned short off[NT / 32][kItems];
 };
 
+template <int NT = kBlock>
 struct GateShared {
-  long long delta[kBlock / 32];
-  unsigned long long ac[kBlock / 32];
+  long long delta[NT / 32];
+  unsigned long long ac[NT / 32];
   unsigned nstage;
   unsigned err;
   unsigned long long base;
@@ -61,13 +63,13 @@ struct GateShared {
 // file comment).  Births go to dense positions T0 + atomicAdd(cnt_slot).
 // The block's live-count change is added to *dlt_slot and its anticommuting
 // count to ctl->ac_total.  Ends with the block's threads synchronised.
-template <int W>
+template <int W, int NT>
 __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const GateArgs& g,
                                           uint64_t T0, unsigned long long* cnt_slot,
-                                          long long* dlt_slot, GateStage<W>& stage,
-                                          GateList<W>& list, GateShared& sh) {
-  constexpr int kWarps = kBlock / 32;
-  constexpr int kU = GateList<W>::kU;
+                                          long long* dlt_slot, GateStage<W, NT>& stage,
+                                          GateList<W, NT>& list, GateShared<NT>& sh) {
+  constexpr int kWarps = NT / 32;
+  constexpr int kU = GateList<W, NT>::kU;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const unsigned lanes_below = (1u << lane) - 1u;
@@ -81,7 +83,7 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
   unsigned long long n_ac = 0;  // live anticommuting terms (for the byte model)
   unsigned err = 0;
   // Block b takes the contiguous range [T0 b / G, T0 (b+1) / G) and splits it
-  // into nt equal tiles of at most kBlock * kU strings, each split equally
+  // into nt equal tiles of at most NT * kU strings, each split equally
   // over the warps: every block does the same number of equally sized tiles,
   // so blocks reach the grid barrier together, and a small table spreads one
   // string per lane over all warps.  nt is block-uniform, so every lane of a
@@ -89,7 +91,7 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
   const uint64_t G = gridDim.x;
   const uint64_t b0 = T0 * blockIdx.x / G;
   const uint64_t Rn = T0 * (blockIdx.x + 1) / G - b0;
-  constexpr uint64_t kTileMax = (uint64_t)kBlock * kU;
+  constexpr uint64_t kTileMax = (uint64_t)NT * kU;
   const uint64_t nt = (Rn + kTileMax - 1) / kTileMax;
   auto warp_range = [&](uint64_t tt, uint64_t& ws, uint64_t& we) {
     const uint64_t ts = b0 + Rn * tt / nt, te = b0 + Rn * (tt + 1) / nt;
@@ -233,7 +235,7 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
         if (lane == leader) b0 = atomicAdd(&sh.nstage, (unsigned)__popc(ballot));
         b0 = __shfl_sync(kFull, b0, leader);
         const unsigned pos = b0 + __popc(ballot & lanes_below);
-        const bool staged = want && pos < (unsigned)GateStage<W>::kCap;
+        const bool staged = want && pos < (unsigned)GateStage<W, NT>::kCap;
         const bool direct = want && !staged;
         if (staged) {
 #pragma unroll
@@ -267,22 +269,36 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
   asm volatile("griddepcontrol.launch_dependents;");
 
   __syncthreads();
-  const unsigned nst = min(sh.nstage, (unsigned)GateStage<W>::kCap);
+  const unsigned nst = min(sh.nstage, (unsigned)GateStage<W, NT>::kCap);
   if (nst) {
+    // The block's positions are reserved while its births claim their index
+    // slots, so the two round trips overlap.  A claimed slot holds the
+    // pending position until it is published below: lookups of this gate only
+    // accept positions below T0, and births are never looked up by the gate
+    // that creates them, so neither ordering matters.
     if (threadIdx.x == 0) sh.base = T0 + atomicAdd(cnt_slot, (unsigned long long)nst);
+    for (unsigned k = threadIdx.x; k < nst; k += NT) {
+      Key<W> R;
+#pragma unroll
+      for (int j = 0; j < 2 * W; ++j) R.w[j] = stage.key[k][j];
+      const uint64_t h = key_hash(R);
+      stage.slot[k] = index_claim_pending(t, h & t.imask, tag_of(h), err);
+    }
     __syncthreads();
-    // births are never looked up by the gate that creates them, so their
-    // keys and index slots need no ordering between each other
-    for (unsigned k = threadIdx.x; k < nst; k += kBlock) {
+    for (unsigned k = threadIdx.x; k < nst; k += NT) {
       const uint64_t idx = sh.base + k;
+      const uint64_t sl = stage.slot[k];
       if (idx < t.cap) {
         Key<W> R;
 #pragma unroll
         for (int j = 0; j < 2 * W; ++j) R.w[j] = stage.key[k][j];
         st_key<W>(t.keys, idx, R);
         t.coef[idx] = stage.coef[k];
-        const uint64_t h = key_hash(R);
-        index_claim(t, h & t.imask, ((uint64_t)tag_of(h) << 32) | idx, err);
+        if (sl <= t.imask) {  // this thread owns the claimed slot
+          const uint64_t h = key_hash(R);
+          reinterpret_cast<unsigned long long*>(t.index)[sl] =
+              ((unsigned long long)tag_of(h) << 32) | idx;
+        }
       } else {
         err |= kErrAppend;
       }
@@ -307,7 +323,10 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
     // fire-and-forget reductions: no block waits for another
     if (d) atomicAdd(reinterpret_cast<unsigned long long*>(dlt_slot), (unsigned long long)d);
     if (a) atomicAdd(&ctl->ac_total, a);
-    if (sh.err) atomicOr(&ctl->error, sh.err);
+    if (sh.err) {
+      atomicOr(&ctl->error, sh.err);
+      atomicOr(&ctl->gerr[cnt_slot - ctl->cnt], sh.err);
+    }
     sh.nstage = 0;
     sh.err = 0;
   }
@@ -319,9 +338,9 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
 template <int W>
 __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict__ tabp,
                                                       DevCtl* __restrict__ ctl, GateArgs g) {
-  __shared__ GateStage<W> stage;
-  __shared__ GateList<W> list;
-  __shared__ GateShared sh;
+  __shared__ GateStage<W, kBlock> stage;
+  __shared__ GateList<W, kBlock> list;
+  __shared__ GateShared<kBlock> sh;
   const unsigned gid = g.gate_id;
   const int slot = (int)(gid % 3u), prev = (int)((gid + 2u) % 3u), next = (int)((gid + 1u) % 3u);
   // With programmatic dependent launch this kernel may already be resident
@@ -341,6 +360,7 @@ __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict
       ctl->live_base[slot] = L0;
       ctl->cnt[next] = 0;
       ctl->dlt[next] = 0;
+      ctl->gerr[next] = 0;
       atomicAdd(&ctl->updates, (double)L0);
       atomicAdd(&ctl->gates_done, 1ull);
       // births R = Q xor P add at most P's letters to the occupancy masks
@@ -359,7 +379,7 @@ __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict
     return;
   }
   __syncthreads();
-  gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
+  gate_pass<W, kBlock>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
 }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -377,17 +397,18 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 }
 
 __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_ok,
-                                          unsigned limit) {
+                                          unsigned limit, unsigned gate) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
     red_release_add(&ctl->bar_root, 1u);
-    unsigned spins = 0;
-    while ((int)(ld_acquire_u32(&ctl->bar_root) - target) < 0) {
-      if (++spins > limit) {
+    const unsigned long long deadline = wait_deadline(limit);
+    unsigned seen;
+    while ((int)((seen = ld_acquire_u32(&ctl->bar_root)) - target) < 0) {
+      if (global_ns() > deadline) {
         ok = 0;
-        atomicOr(&ctl->error, kErrTimeout);
+        note_timeout(ctl, 1u, gate, seen, target);
         break;
       }
       __nanosleep(16);
@@ -402,7 +423,8 @@ __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_
 // registers and consecutive gates are separated by a grid barrier instead of
 // a kernel boundary.  Gate ids and the capacity stall are the same as for
 // gate_kernel, so chain_init / chain_finish serve both: on leaving, block 0
-// records the table size where chain_finish reads it.
+// records the table size in the control block's exit record, which
+// chain_finish reads.
 //
 // Occupancy test: every block keeps the OR of the x and of the z words of all
 // stored strings (read from the control block, then widened by the letters
@@ -413,15 +435,29 @@ __device__ __forceinline__ bool grid_sync(DevCtl* ctl, unsigned& target, int& s_
 // or a barrier.  Its updates are counted as for any other gate (and, apart,
 // as skipped).  Executed gates take the counter slots by their ordinal e in
 // this launch.
-template <int W>
-__global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
+template <int W, int NT>
+struct LayerSmem {
+  GateStage<W, NT> stage;
+  GateList<W, NT> list;
+  GateShared<NT> sh;
+  GateArgs gate[2];  // current gate and the prefetched next one
+  int ok;
+};
+
+// Blocks of NT threads: 256 (four or two per SM) or 1024 (one per SM: a
+// quarter of the blocks take part in each barrier and each birth
+// reservation).  Shared memory is dynamic (LayerSmem).
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : ((W == 1) ? 4 : 2))
     layer_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
                  const GateArgs* __restrict__ gates, unsigned n_gates) {
-  __shared__ GateStage<W> stage;
-  __shared__ GateList<W> list;
-  __shared__ GateShared sh;
-  __shared__ GateArgs s_gate[2];  // current gate and the prefetched next one
-  __shared__ int s_ok;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LayerSmem<W, NT>& S = *reinterpret_cast<LayerSmem<W, NT>*>(smem_raw);
+  GateStage<W, NT>& stage = S.stage;
+  GateList<W, NT>& list = S.list;
+  GateShared<NT>& sh = S.sh;
+  GateArgs* s_gate = S.gate;
+  int& s_ok = S.ok;
   const DevTable t = *tabp;
   const unsigned first = __ldcg(&ctl->first_gate);
   const int q0 = (int)((first + 2u) % 3u);
@@ -442,9 +478,9 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
   auto fetch_args = [&](unsigned gid, int buf) {
     const unsigned* src = reinterpret_cast<const unsigned*>(gates + gid);
     unsigned* dst = reinterpret_cast<unsigned*>(&s_gate[buf]);
-    for (unsigned k = threadIdx.x; k < sizeof(GateArgs) / 4; k += kBlock) dst[k] = __ldg(src + k);
+    for (unsigned k = threadIdx.x; k < sizeof(GateArgs) / 4; k += NT) dst[k] = __ldg(src + k);
   };
-  if (__ldcg(&ctl->stall) != 0u || __ldcg(&ctl->error) != 0u) return;  // uniform
+  if (__ldcg(&ctl->entry_stop) != 0u) return;  // written before the launch: uniform
   if (first < n_gates) fetch_args(first, 0);
   unsigned e = 0;  // gates executed by this launch
   int buf = 0;
@@ -477,10 +513,11 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->cnt[next] = 0;
       ctl->dlt[next] = 0;
+      ctl->gerr[next] = 0;
       atomicAdd(&ctl->updates, (double)L0);
       atomicAdd(&ctl->gates_done, 1ull);
     }
-    gate_pass<W>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
+    gate_pass<W, NT>(t, ctl, g, T0, &ctl->cnt[slot], &ctl->dlt[slot], stage, list, sh);
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       ox[j] |= g.px[j];
@@ -492,22 +529,21 @@ __global__ void __launch_bounds__(kBlock, (W == 1) ? 4 : 2)
       // fence and the block barrier, are all the next gate depends on
       __threadfence();
       __syncthreads();
-    } else if (!grid_sync(ctl, target, s_ok, wlimit)) {
+    } else if (!grid_sync(ctl, target, s_ok, wlimit, gid)) {
       return;
     }
     T0 += __ldcg(&ctl->cnt[slot]);
     L0 += __ldcg(&ctl->dlt[slot]);
     ++e;
-    if (__ldcg(&ctl->error) != 0u) return;  // uniform after the barrier
+    if (__ldcg(&ctl->gerr[slot]) != 0u) return;  // written by this gate only: uniform
   }
-  // the state after the last gate applied, where chain_finish looks for it
-  // (slot of gate end - 1), and the widened occupancy masks
+  // the state after the last gate applied, in the exit record (not a gate
+  // slot: slower blocks may still be reading the slot of the last gate when
+  // block 0 gets here), and the widened occupancy masks
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int q = (int)((end + 2u) % 3u);
-    ctl->base[q] = T0;
-    ctl->cnt[q] = 0;
-    ctl->live_base[q] = L0;
-    ctl->dlt[q] = 0;
+    ctl->exit_terms = T0;
+    ctl->exit_live = L0;
+    ctl->exit_set = 1u;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       ctl->occ[j] = ox[j];
@@ -538,16 +574,25 @@ __global__ void chain_init_kernel(DevCtl* ctl, unsigned first_gate) {
   for (int k = 0; k < 3; ++k) {
     ctl->cnt[k] = 0;
     ctl->dlt[k] = 0;
+    ctl->gerr[k] = 0;
   }
   ctl->stall = 0;
   ctl->first_gate = first_gate;
+  ctl->exit_set = 0;
+  ctl->entry_stop = ctl->error != 0u ? 1u : 0u;
 }
 
 __global__ void chain_finish_kernel(DevCtl* ctl, unsigned n_gates) {
-  const unsigned end = ctl->stall ? ctl->stall - 1u : n_gates;  // first gate not applied
-  const int q = (int)((end + 2u) % 3u);                         // slot of gate end-1
-  ctl->n_terms = ctl->base[q] + ctl->cnt[q];
-  ctl->n_live = ctl->live_base[q] + ctl->dlt[q];
+  if (ctl->exit_set) {
+    ctl->n_terms = ctl->exit_terms;
+    ctl->n_live = ctl->exit_live;
+  } else {
+    const unsigned end = ctl->stall ? ctl->stall - 1u : n_gates;  // first gate not applied
+    const int q = (int)((end + 2u) % 3u);                         // slot of gate end-1
+    ctl->n_terms = ctl->base[q] + ctl->cnt[q];
+    ctl->n_live = ctl->live_base[q] + ctl->dlt[q];
+  }
+  ctl->after_terms = ctl->n_terms;
 }
 
 // ------------------------------------------------------ merge / insert
@@ -602,14 +647,17 @@ __global__ void __launch_bounds__(kBlock)
         s = old;
       }
       if ((uint32_t)(s >> 32) == tag) {
-        unsigned spins = 0;
-        while ((uint32_t)s == kPendingIdx && spins < wlimit) {
-          ++spins;
-          __nanosleep(64);
-          s = *reinterpret_cast<volatile unsigned long long*>(index + pos);
+        // read the slot again with acquire semantics before using its position
+        s = ld_acquire_u64(index + pos);
+        if ((uint32_t)s == kPendingIdx) {
+          const unsigned long long deadline = wait_deadline(wlimit);
+          while ((uint32_t)s == kPendingIdx && global_ns() <= deadline) {
+            __nanosleep(64);
+            s = ld_acquire_u64(index + pos);
+          }
         }
         if ((uint32_t)s == kPendingIdx) {
-          err |= kErrTimeout;
+          note_timeout(ctl, 3u, 0u, (unsigned)pos, 0u);
           done = true;
           break;
         }
@@ -912,43 +960,76 @@ cudaError_t launch_gate_w(int grid, cudaStream_t s, const DevTable* tab, DevCtl*
   return cudaLaunchKernelEx(&cfg, gate_kernel<W>, tab, ctl, g);
 }
 
-template <int W>
+// The layer kernel's dynamic shared memory must be allowed above 48 KB once
+// per instantiation (and before an occupancy query).
+template <int W, int NT>
+cudaError_t layer_smem_setup() {
+  static cudaError_t done = cudaFuncSetAttribute(
+      layer_kernel<W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)sizeof(LayerSmem<W, NT>));
+  return done;
+}
+
+template <int W, int NT>
 cudaError_t launch_layer_w(int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
                            const GateArgs* gates, unsigned n_gates) {
+  cudaError_t e = layer_smem_setup<W, NT>();
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = 0;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(LayerSmem<W, NT>);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, layer_kernel<W>, tab, ctl, gates, n_gates);
+  return cudaLaunchKernelEx(&cfg, layer_kernel<W, NT>, tab, ctl, gates, n_gates);
 }
 
-cudaError_t launch_layer(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,
-                         const GateArgs* gates, unsigned n_gates) {
+template <int W, int NT>
+int layer_bps_w() {
+  int nb = 0;
+  if (layer_smem_setup<W, NT>() != cudaSuccess) return 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, layer_kernel<W, NT>, NT, sizeof(LayerSmem<W, NT>));
+  return (e == cudaSuccess && nb > 0) ? nb : 0;
+}
+
+cudaError_t launch_layer(int W, int threads, int grid, cudaStream_t s, const DevTable* tab,
+                         DevCtl* ctl, const GateArgs* gates, unsigned n_gates) {
+  if (threads == 1024) {
+    switch (W) {
+      case 1: return launch_layer_w<1, 1024>(grid, s, tab, ctl, gates, n_gates);
+      case 2: return launch_layer_w<2, 1024>(grid, s, tab, ctl, gates, n_gates);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (W) {
-    case 1: return launch_layer_w<1>(grid, s, tab, ctl, gates, n_gates);
-    case 2: return launch_layer_w<2>(grid, s, tab, ctl, gates, n_gates);
-    case 3: return launch_layer_w<3>(grid, s, tab, ctl, gates, n_gates);
-    case 4: return launch_layer_w<4>(grid, s, tab, ctl, gates, n_gates);
+    case 1: return launch_layer_w<1, kBlock>(grid, s, tab, ctl, gates, n_gates);
+    case 2: return launch_layer_w<2, kBlock>(grid, s, tab, ctl, gates, n_gates);
+    case 3: return launch_layer_w<3, kBlock>(grid, s, tab, ctl, gates, n_gates);
+    case 4: return launch_layer_w<4, kBlock>(grid, s, tab, ctl, gates, n_gates);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int layer_blocks_per_sm(int W) {
-  int nb = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (W) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<1>, kBlock, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<2>, kBlock, 0); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<3>, kBlock, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, layer_kernel<4>, kBlock, 0); break;
+int layer_blocks_per_sm(int W, int threads) {
+  if (threads == 1024) {
+    switch (W) {
+      case 1: return layer_bps_w<1, 1024>();
+      case 2: return layer_bps_w<2, 1024>();
+      default: return 0;
+    }
   }
-  return (e == cudaSuccess && nb > 0) ? nb : 0;
+  switch (W) {
+    case 1: return layer_bps_w<1, kBlock>();
+    case 2: return layer_bps_w<2, kBlock>();
+    case 3: return layer_bps_w<3, kBlock>();
+    case 4: return layer_bps_w<4, kBlock>();
+    default: return 0;
+  }
 }
 
 cudaError_t launch_gate(int W, int grid, cudaStream_t s, const DevTable* tab, DevCtl* ctl,

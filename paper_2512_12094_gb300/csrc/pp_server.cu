@@ -7,7 +7,8 @@
 // arrives while others run starts as soon as a slot and memory are free, and
 // the kernels of different jobs overlap on the device.  A job runs in its own
 // context (tables resident on the device for its whole life) whose memory
-// budget is its reservation.
+// budget is its reservation; its layers run as persistent launches on at most
+// 1/slots of the GPU.
 //
 // Reservations follow the jobs' live-term counts.  A job's first reservation
 // is the memory of a table for its observable (unless the job names one).
@@ -79,6 +80,7 @@ struct pp_server {
   size_t default_reserve = 0;
   size_t reserved = 0;  // sum of the reservations of running jobs
   int64_t growing = 0;  // running jobs waiting for a larger reservation
+  int slots = 1;
   int device = 0;
   bool stopping = false;
   uint64_t next_id = 1;
@@ -164,7 +166,6 @@ pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, b
   pp_config cfg = j.cfg;
   cfg.cuda_stream = stream;
   cfg.mem_budget_bytes = j.reserve;
-  cfg.layer_kernel = 0;  // one kernel per gate: jobs on other streams can interleave
   pp_ctx* ctx = nullptr;
   // a reactive increase: twice the reservation; false when the job must stop
   auto grow_or_stop = [&](pp_status& st) {
@@ -184,6 +185,10 @@ pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, b
                    j.coef.data(), &ctx);
     if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
   }
+  // A job's layers run in one persistent launch each, on at most its share of
+  // the GPU, so that the jobs of all slots overlap; a small table runs in a
+  // single block with no grid barrier at all.
+  if (st == PP_OK) ppk::set_grid_share(ctx, s->slots);
   int64_t live_prev = -1;
   for (int l = 0; st == PP_OK && l < j.n_layers; ++l) {
     // proactive: the memory the context holds, scaled by the live-term
@@ -288,6 +293,7 @@ pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_jo
   }
   pp_server* s = new pp_server();
   s->budget = mem_budget_bytes;
+  s->slots = slots;
   s->default_reserve = default_job_bytes;  // 0: each job's reservation is estimated
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;

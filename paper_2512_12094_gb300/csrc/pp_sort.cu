@@ -463,6 +463,7 @@ __global__ void __launch_bounds__(kST)
   const T teps = (T)eps;  // liveness is decided in the storage type, as by the hash merge
   unsigned err = 0;
   long long live = 0;
+  OccAcc<W> occ;
   const uint64_t wstride = (uint64_t)gridDim.x * kSWarps;
   for (uint64_t r = (uint64_t)blockIdx.x * kSWarps + (threadIdx.x >> 5); r < total; r += wstride) {
     const uint64_t j0 = sb.headpos[r];
@@ -498,6 +499,7 @@ __global__ void __launch_bounds__(kST)
     if (lane == 0) {
       const Key<W> K = unpack_key<W, KW>(sb.k0[buf][j0], KW == 2 ? sb.k1[buf][j0] : 0ull);
       st_key<W>(dst.keys, idx, K);
+      occ.add(K);
       dst.alive[idx] = any ? 1 : 0;
       live += any;
       if (with_index) {
@@ -508,6 +510,7 @@ __global__ void __launch_bounds__(kST)
   }
   if (lane == 0 && live)
     atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_live), (unsigned long long)live);
+  occ.flush(ctl);
   if (err) atomicOr(&ctl->error, err);
 }
 

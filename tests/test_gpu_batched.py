@@ -179,3 +179,32 @@ def test_batched_fp32_per_gate_noise_within_fp32_tolerance(group):
     bloch = pi.neel_state(n).bloch
     got, want = prop.expect(bloch), st.expect(bloch)
     assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-6)
+
+
+@pytest.mark.parametrize("f32,noise", [(False, 0.0), (False, 0.03), (True, 0.0)])
+def test_batched_launch_paths_agree(f32, noise):
+    """All gates of a layer in one persistent cooperative launch, and one kernel
+    per gate replayed from CUDA graphs, give the same rows bit for bit and the
+    same update statistics (gates the occupancy test skips included)."""
+    n, B = 14, 40
+    angles = pi.batched_ring_angles(B, 11)
+    gx, gz, _ = pi.Circuit(n, [pi.ring_layer(n, 0.0, 0.0, 0.0)]).gate_arrays(0)
+    th = ring_theta(n, angles)
+    x, z, c = pi.mean_z(n).arrays()
+    coef = np.repeat(c[:, None], B, axis=1)
+    runs, stats = [], []
+    for layer_kernel in (True, False):
+        prop = pp.Propagator(n, x, z, coef, eps=1e-4, max_weight=6, batch=B, f32=f32,
+                             layer_kernel=layer_kernel,
+                             noise_mode=pp.NOISE_PER_GATE if noise else pp.NOISE_NONE,
+                             noise_p=noise)
+        for _ in range(3):
+            prop.apply_layer(gx, gz, th, boundary=False)
+        runs.append(rows_dict(*prop.export()))
+        st = prop.stats()
+        stats.append((st["gate_updates"], st["anticommuting_terms"], st["gates_applied"]))
+        prop.close()
+    assert stats[0] == stats[1]
+    assert set(runs[0]) == set(runs[1]) and len(runs[0]) > 50
+    for k in runs[0]:
+        np.testing.assert_array_equal(runs[0][k], runs[1][k])

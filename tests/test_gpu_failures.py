@@ -1,7 +1,7 @@
 """Failure detection without a GPU fault.
 
-* Every device wait is bounded.  A context whose bound is one poll makes the
-  grid barrier of a multi-block layer run out: the kernel records the timeout
+* Every device wait is bounded.  A context whose bound is one microsecond
+  makes the grid barrier of a multi-block layer run out: the kernel records the timeout
   and returns, the call reports PP_ERR_TIMEOUT, the context can be destroyed,
   and the next context on the same GPU computes the oracle's result.
 * Device allocations can be made to fail on the host
@@ -47,7 +47,7 @@ def oracle_after(wl, layers):
     return st.as_dict()
 
 
-def test_grid_barrier_wait_runs_out_with_a_one_poll_bound():
+def test_grid_barrier_wait_runs_out_with_a_one_microsecond_bound():
     wl = pi.config1_ring(n=20, steps=6, eps=0.0, max_weight=6)
     ox, oz, oc = wl.observable.arrays()
     cfg = pp.pp_config_default(n_qubits=20, max_weight=6, wait_limit=1)

@@ -116,15 +116,16 @@ def test_truncation_bitexact(eps, wmax):
 
 @pytest.mark.parametrize("symmetry", [0, 1])
 def test_launch_paths_agree(symmetry):
-    """Cooperative layer kernel, per-gate kernels from CUDA graphs (PDL) and
-    per-gate direct launches give bit-identical tables and the same update
+    """Cooperative layer kernel (blocks of 256 and of 1024 threads), per-gate
+    kernels from CUDA graphs (PDL) and per-gate direct launches give
+    bit-identical tables and the same update
     statistics (live terms and live anticommuting terms entering each gate,
     counted from values before the gate, so no path depends on timing)."""
     wl = pi.config1_ring(n=32 if symmetry == 0 else 16, steps=5, eps=1e-4 if symmetry == 0 else 1e-5,
                          max_weight=10 if symmetry == 0 else 8)
     runs, stats = [], []
-    for kw in (dict(layer_kernel=True), dict(layer_kernel=False, use_graphs=True),
-               dict(layer_kernel=False, use_graphs=False), dict(layer_kernel=True)):
+    for kw in (dict(layer_kernel=True, block_threads=256), dict(layer_kernel=False, use_graphs=True),
+               dict(layer_kernel=False, use_graphs=False), dict(layer_kernel=True, block_threads=1024)):
         p = pp.Propagator.from_workload(wl, symmetry=symmetry, **kw)
         p.run(wl)
         runs.append(as_dict(*p.export()))

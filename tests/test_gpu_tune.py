@@ -42,7 +42,9 @@ def test_tuned_context_continues_like_untuned(group, layer_kernel):
         if k == 2:  # a table of some size to time
             scale = pp.pp_tune(tuned.ctx, g, th)
             assert scale in (0.5, 1.0, 2.0, 4.0)
-            assert tuned.stats()["grid_scale"] == scale
+            st = tuned.stats()
+            assert st["grid_scale"] == scale
+            assert st["index_factor"] in (1.5, 3.0) and st["persistent"] in (0, 1)
             a, b = tuned.stats(), plain.stats()
             for key in ("gate_updates", "anticommuting_terms", "gates_applied", "live_terms"):
                 assert a[key] == b[key], key

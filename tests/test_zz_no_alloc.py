@@ -73,3 +73,44 @@ def test_noalloc_merge_rejects_oversized_input():
         pp.pp_merge_terms_noalloc(16, 0, 524289, 1, 1, 1, 1, m_dev)
     assert e.value.status == 1
     assert "524288" in str(e.value)
+
+
+def test_noalloc_merge_allocates_nothing_and_replays_in_a_cuda_graph():
+    """Free device memory is the same before and after the call, and the call
+    (after a first call on the device, which looks up the scratch address) can
+    be captured into a CUDA graph in global capture mode and replayed on new
+    inputs: each replay matches pp_merge_terms on those inputs."""
+    import torch
+    n, group, m = 24, 1, 4000
+    keys, coef, W = _keys(n, m, 11)
+    d_k = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_c = torch.from_numpy(coef).cuda()
+    out_k, out_c = torch.empty_like(d_k), torch.empty_like(d_c)
+    m_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pp.pp_merge_terms_noalloc(n, group, m, d_k, d_c, out_k, out_c, m_dev, stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pp.pp_merge_terms_noalloc(n, group, m, d_k, d_c, out_k, out_c, m_dev, stream)
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="global"):
+        pp.pp_merge_terms_noalloc(n, group, m, d_k, d_c, out_k, out_c, m_dev, stream)
+    for seed in (12, 13):
+        keys2, coef2, _ = _keys(n, m, seed)
+        d_k.copy_(torch.from_numpy(keys2.view(np.int64)))
+        d_c.copy_(torch.from_numpy(coef2))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref_k, ref_c = torch.empty_like(d_k), torch.empty_like(d_c)
+        m_ref = pp.pp_merge_terms(n, group, m, d_k, d_c, ref_k, ref_c)
+        m_got = int(m_dev.cpu()[0])
+        assert m_got == m_ref
+        got = _as_dict(out_k[:m_got].cpu().numpy().view(np.uint64), out_c[:m_got].cpu().numpy())
+        want = _as_dict(ref_k[:m_ref].cpu().numpy().view(np.uint64), ref_c[:m_ref].cpu().numpy())
+        assert set(got) == set(want)
+        assert max(abs(got[k] - want[k]) for k in want) < 1e-12
