@@ -126,6 +126,12 @@ typedef struct {
                               it gives up: the kernel records the failure and returns, and the
                               call reports PP_ERR_TIMEOUT; 0 = the default, 30 s (a gate over
                               gigabytes of batched rows takes seconds).  >= 0. */
+  double room_factor;      /* headroom a layer asks for before its first gate: room for
+                              2 x room_factor x (the previous layer's growth) times the
+                              stored terms, and at least twice them; a layer that outgrows
+                              it stops part way, grows the table and goes on (pp_stats_t
+                              stalls).  0 = the default, 1.25; smaller values trade
+                              stalls for memory.  >= 0. */
 } pp_config;
 
 typedef struct pp_ctx pp_ctx;
@@ -154,6 +160,7 @@ typedef struct {
   int64_t persistent;      /* 1: layers run in one persistent kernel, 0: one kernel per gate */
   int64_t block_threads;   /* threads per block of the kernels that apply gates */
   int64_t stalls;          /* times a layer stopped part way for room, grew the table and went on */
+  int64_t index_slots;     /* hash index slots of the active table (a power of two) */
 } pp_stats_t;
 
 /* Fill *cfg with defaults: n_qubits = 0 (must be set), no symmetry, batch 1,

@@ -95,7 +95,8 @@ class pp_config(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("check_symmetry", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("profile_kernels", ctypes.c_int),
                 ("layer_kernel", ctypes.c_int), ("merge_method", ctypes.c_int),
-                ("block_threads", ctypes.c_int), ("wait_limit", ctypes.c_int)]
+                ("block_threads", ctypes.c_int), ("wait_limit", ctypes.c_int),
+                ("room_factor", ctypes.c_double)]
 
 
 class pp_pauli(ctypes.Structure):
@@ -129,7 +130,8 @@ class pp_stats_t(ctypes.Structure):
                 ("gate_kernels_timed", ctypes.c_int64), ("grid_scale", ctypes.c_double),
                 ("skipped_updates", ctypes.c_double), ("gates_skipped", ctypes.c_int64),
                 ("index_factor", ctypes.c_double), ("persistent", ctypes.c_int64),
-                ("block_threads", ctypes.c_int64), ("stalls", ctypes.c_int64)]
+                ("block_threads", ctypes.c_int64), ("stalls", ctypes.c_int64),
+                ("index_slots", ctypes.c_int64)]
 
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -471,7 +473,7 @@ class Propagator:
     def __init__(self, n_qubits, x, z, coef, symmetry=SYM_NONE, eps=0.0, max_weight=-1,
                  noise_mode=NOISE_NONE, noise_p=0.0, budget=0, stream=None, use_graphs=True,
                  check_symmetry=True, profile=False, layer_kernel=True, batch=1, f32=False,
-                 merge_method=MERGE_HASH, block_threads=0, wait_limit=0):
+                 merge_method=MERGE_HASH, block_threads=0, wait_limit=0, room_factor=0.0):
         self.n = n_qubits
         self.cfg = pp_config_default(n_qubits=n_qubits, symmetry=symmetry, coeff_eps=eps,
                                      max_weight=max_weight, noise_mode=noise_mode,
@@ -481,7 +483,8 @@ class Propagator:
                                      profile_kernels=int(profile),
                                      layer_kernel=int(layer_kernel), batch=int(batch),
                                      coef_type=1 if f32 else 0, merge_method=int(merge_method),
-                                     block_threads=int(block_threads), wait_limit=int(wait_limit))
+                                     block_threads=int(block_threads), wait_limit=int(wait_limit),
+                                     room_factor=float(room_factor))
         self.batch = int(batch)
         self.ctx = pp_create(self.cfg, x, z, coef)
         self._packed = {}

@@ -243,7 +243,10 @@ void dfree(pp_ctx* c, void* p, size_t bytes) {
 // Index slots per dense entry of capacity: the index is a power of two of at
 // least index_factor (1.5 unless pp_tune chose another) times the capacity, so
 // its load stays below 2/3 even when the table is full (a gate stalls before
-// that can happen) and is about 1/4 at a layer start.
+// that can happen) and is about 1/4 at a layer start.  (An index sized for
+// the stored entries instead, at up to half load, was measured slower: the
+// longer probe chains of births' slot claims, one atomic round trip each,
+// cost more than the smaller footprint saved in lookups.)
 uint64_t index_cap_for(const pp_ctx* c, uint64_t cap) {
   return next_pow2((uint64_t)std::ceil(c->index_factor * (double)cap));
 }
@@ -280,12 +283,12 @@ pp_status alloc_buf(pp_ctx* c, Buf& b, uint64_t cap) {
 }
 
 DevTable desc_of(const pp_ctx* c, const Buf& b) {
-  DevTable t;
+  DevTable t = {};
   t.keys = b.keys;
   t.coef = b.coef;
   t.index = b.index;
   t.cap = b.cap;
-  t.imask = b.icap - 1;
+  t.imask = b.icap ? b.icap - 1 : 0;
   t.rows = b.rows;
   t.alive = b.alive;
   t.B = c->B;
@@ -701,6 +704,8 @@ pp_status validate_config(const pp_config* cfg) {
   if (cfg->merge_method != PP_MERGE_HASH && cfg->merge_method != PP_MERGE_SORT)
     return fail(PP_ERR_ARG, "unknown merge_method");
   if (cfg->wait_limit < 0) return fail(PP_ERR_ARG, "wait_limit must be >= 0");
+  if (!(cfg->room_factor >= 0.0) || !std::isfinite(cfg->room_factor))
+    return fail(PP_ERR_ARG, "room_factor must be finite and >= 0");
   if (cfg->block_threads != 0 && cfg->block_threads != 256 && cfg->block_threads != 1024)
     return fail(PP_ERR_ARG, "block_threads must be 0, 256 or 1024");
   return PP_OK;
@@ -1226,9 +1231,11 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
                               desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
     c->launches += 1;
   }
-  // room for 2.5 times the growth the previous layer showed (at least doubling)
+  // room for 2 x room_factor (1.25 unless configured) times the growth the
+  // previous layer showed, and at least twice the stored terms
+  const double rf = c->cfg.room_factor > 0.0 ? c->cfg.room_factor : 1.25;
   const uint64_t factor =
-      std::max<uint64_t>(2, (uint64_t)std::ceil(2.0 * 1.25 * std::max(1.0, c->last_growth)));
+      std::max<uint64_t>(2, (uint64_t)std::ceil(2.0 * rf * std::max(1.0, c->last_growth)));
   PP_TRY(make_room(c, factor));
   const uint64_t n_start = std::max<uint64_t>(c->n_terms, 1);
   const uint64_t est = std::max<uint64_t>(c->n_terms + c->n_terms / 4, 1);
@@ -1237,13 +1244,22 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   int grid_b = 1;
   // batched rows take a warp B/32 steps per pair, so they get B/32 times the blocks
   const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
-  if (layered) {
-    // persistent: one string per thread per pass, never more blocks than can
-    // be co-resident (the grid barrier needs all of them)
+  // persistent: one string per thread per pass, never more blocks than can
+  // be co-resident (the grid barrier needs all of them).  Batched rows size
+  // the grid for the table the layer is expected to reach (the previous
+  // layer's growth), since their row work dwarfs the scan and a table that
+  // grows tenfold within the layer would otherwise run on a tenth of the
+  // blocks; a relaunch after a stall sizes it again.
+  auto layered_grid = [&](uint64_t n_now) {
     const int nt = c->batched ? kBlock : c->layer_threads;
-    const uint64_t want = (uint64_t)std::ceil((double)(est * rowf) * c->grid_scale / nt);
+    const double grow = c->batched ? std::max(1.25, c->last_growth) : 1.25;
+    const double e = std::max(1.0, (double)n_now * grow);
+    const uint64_t want = (uint64_t)std::ceil(e * (double)rowf * c->grid_scale / nt);
     const uint64_t room = std::max<uint64_t>(1, (uint64_t)c->sms * c->layer_bps / c->grid_share);
-    grid_b = (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), room);
+    return (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), room);
+  };
+  if (layered) {
+    grid_b = layered_grid(c->n_terms);
   } else {
     // a power of two so that captured graphs are reused
     while ((double)grid_b * kBlock < (double)(est * rowf) * c->grid_scale) grid_b <<= 1;
@@ -1307,6 +1323,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       c->n_terms = c->h_ctl->n_terms;
       c->n_live = c->h_ctl->n_live;
       PP_TRY(make_room(c, std::max<uint64_t>(factor, 4)));
+      if (layered) grid_b = layered_grid(c->n_terms);
       first = end;
     }
   }
@@ -1338,6 +1355,7 @@ pp_status pp_config_default(pp_config* cfg) {
   cfg->layer_kernel = 1;
   cfg->merge_method = PP_MERGE_HASH;
   cfg->wait_limit = 0;
+  cfg->room_factor = 0.0;
   cfg->block_threads = 0;
   return PP_OK;
 }
@@ -1836,6 +1854,10 @@ pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
   out->persistent = (c->cfg.layer_kernel && c->layer_bps > 0) ? 1 : 0;
   out->block_threads = out->persistent ? (c->batched ? kBlock : c->layer_threads) : kBlock;
   out->stalls = c->stalls;
+  {
+    const Buf& a = c->buf[c->active];
+    out->index_slots = (int64_t)a.icap;
+  }
   return PP_OK;
 }
 
@@ -1890,7 +1912,7 @@ pp_status pp_merge_terms(int n_qubits, int symmetry, int64_t m, const uint64_t* 
     cudaFreeAsync(index, s);
     return cuda_fail(e, "cudaMallocAsync");
   }
-  DevTable dst;
+  DevTable dst = {};
   dst.keys = keys_out;
   dst.coef = coef_out;
   dst.index = index;
@@ -1937,7 +1959,7 @@ pp_status pp_merge_terms_sorted(int n_qubits, int symmetry, int64_t m, const uin
     cudaFreeAsync(scratch, s);
     return cuda_fail(e, "cudaMallocAsync");
   }
-  DevTable dst;
+  DevTable dst = {};
   memset(&dst, 0, sizeof(dst));
   dst.keys = keys_out;
   dst.coef = coef_out;

@@ -78,8 +78,8 @@ struct BatchedShared {
 // together instead of one column at a time.
 constexpr int kColU = 8;
 
-// One gate over the rows [0, T0) by one block.  The block takes kBlock
-// strings at a time (block-stride); every thread decides its string's action
+// One gate over the rows [0, T0) by one block.  The block takes its equal
+// share of [0, T0), kBlock strings at a time; every thread decides its string's action
 // from the keys, the actions are compacted into a shared queue, and the
 // block's warps take them in turn, each streaming the rows of one action with
 // coalesced loads and stores.  So a chunk with many actions keeps every warp
@@ -101,14 +101,18 @@ __device__ __forceinline__ void gate_pass_batched(const DevTable& t, DevCtl* ctl
   long long delta = 0;
   unsigned long long n_ac = 0;
   unsigned err = 0;
-  const uint64_t bstride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t cbase = (uint64_t)blockIdx.x * kBlock; cbase < T0; cbase += bstride) {
+  // block b takes [T0 b / G, T0 (b+1) / G) in chunks of kBlock strings, so
+  // every block of the grid has strings (and row actions) even when the table
+  // is smaller than the grid times kBlock; the chunk count is block-uniform
+  const uint64_t G = gridDim.x;
+  const uint64_t r0 = T0 * blockIdx.x / G, r1 = T0 * (blockIdx.x + 1) / G;
+  for (uint64_t cbase = r0; cbase < r1; cbase += kBlock) {
     const uint64_t i = cbase + threadIdx.x;
     int act = 0, kq = 0, kr = 0;
     int64_t jr = -1;
     bool aliveQ = false, aliveR = false, neg = false;
     Key<W> R;
-    if (i < T0) {
+    if (i < r1) {
       const Key<W> Q = ld_key_cg<W>(t.keys, i);
       aliveQ = __ldcg(t.alive + i) != 0;
       int acnt = 0;
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(kBlock) gate_batched_kernel(const DevTable* __
   const long long L0 = __ldcg(&ctl->live_base[prev]) + __ldcg(&ctl->dlt[prev]);
   bool run = (gid >= __ldcg(&ctl->first_gate)) && (__ldcg(&ctl->stall) == 0u) &&
              (__ldcg(&ctl->error) == 0u);
-  const bool room = 2ull * T0 <= t.cap;
+  const bool room = gate_fits(t, T0);
   if (threadIdx.x == 0) {
     if (blockIdx.x == 0 && run && !room) ctl->stall = gid + 1;
     if (blockIdx.x == 0 && run && room) {
@@ -427,7 +431,7 @@ __device__ __forceinline__ bool grid_sync_b(DevCtl* ctl, unsigned& target, int& 
 // by their ordinal.  On leaving, block 0 records the state in the exit
 // record, which chain_finish reads.
 template <int W, typename T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, W == 1 ? 3 : 2)
     layer_batched_kernel(const DevTable* __restrict__ tabp, DevCtl* __restrict__ ctl,
                          const GateArgs* __restrict__ gates, unsigned n_gates) {
   __shared__ BatchedShared<W, T> sh;
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kBlock)
       }
       continue;
     }
-    if (2ull * T0 > t.cap) {  // the same decision in every block
+    if (!gate_fits(t, T0)) {  // the same decision in every block
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->stall = gid + 1;
       end = gid;
       break;

@@ -52,6 +52,14 @@ __device__ __forceinline__ bool queued_layer_stopped(const DevCtl* ctl) {
          *reinterpret_cast<const volatile unsigned*>(&ctl->error) != 0u;
 }
 
+// Room for one more gate on a table of T0 stored entries: a gate appends at
+// most one birth per string, so the capacity must hold 2 T0 (the index has
+// at least 1.5 slots per entry of capacity).  Every block of a gate takes the
+// same decision from the same T0.
+__device__ __forceinline__ bool gate_fits(const DevTable& t, uint64_t T0) {
+  return 2ull * T0 <= t.cap;
+}
+
 __device__ __forceinline__ unsigned wait_limit_of(const DevCtl* ctl) {
   const unsigned v = *reinterpret_cast<const volatile unsigned*>(&ctl->wait_limit);
   return v ? v : kDefaultWaitLimit;
@@ -784,11 +792,16 @@ __device__ __forceinline__ double ld_coef(const double* c, uint64_t i) { return 
 template <int W>
 __device__ __forceinline__ int64_t index_find_old(const DevTable& t, const Key<W>& k, uint64_t h,
                                                   uint32_t tag, uint64_t T0, unsigned& err,
-                                                  bool load_coef = false, double* c = nullptr) {
+                                                  bool load_coef = false, double* c = nullptr,
+                                                  bool need = true) {
   uint64_t pos = h & t.imask;
   for (uint64_t probe = 0; probe <= t.imask; ++probe) {
     const uint64_t s = __ldcg(reinterpret_cast<const unsigned long long*>(t.index) + pos);
     if (s == 0) return -1;
+    // a caller with nothing to do whether or not the key is stored gives up
+    // here; `need` is evaluated only now, so its own loads overlap the first
+    // slot's
+    if (!need) return -3;
     if ((uint32_t)(s >> 32) == tag) {
       const uint32_t idx = (uint32_t)s;
       if ((uint64_t)idx < T0) {

@@ -175,14 +175,15 @@ __device__ __forceinline__ void gate_pass(const DevTable& t, DevCtl* ctl, const 
         const double cQ = ld_coef(t.coef, i);
         const bool liveQ = !is_dead(cQ);
         // The member of {Q, R} with the pivot bit of P clear owns the pair,
-        // decided from keys only.  Every member looks its partner up without
-        // waiting for its own coefficient (a truncated member with the bit set
-        // then has nothing to do: its partner owns the pair or is absent); the
-        // owner loads the partner's coefficient together with its key.
+        // decided from keys only.  Every member starts its lookup without
+        // waiting for its own coefficient; the owner loads the partner's
+        // coefficient together with its key.
         const bool owner = pw == 0;
         double cRo = 0.0;
         const uint64_t h = key_hash(R);
-        const int64_t jr = index_find_old<W>(t, R, h, tag_of(h), T0, err, owner, &cRo);
+        // a truncated non-owner has nothing to do (its partner owns the pair
+        // or is absent, and it has no birth): its lookup stops at the first slot
+        const int64_t jr = index_find_old<W>(t, R, h, tag_of(h), T0, err, owner, &cRo, owner || liveQ);
         const bool neg = sigma_of<W>(g, Qk) < 0;  // i P Q = -R
         const double cR = (jr >= 0 && owner) ? cRo : 0.0;
         // live anticommuting strings, counted from values before the gate: the
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kBlock) gate_kernel(const DevTable* __restrict
   const long long L0 = __ldcg(&ctl->live_base[prev]) + __ldcg(&ctl->dlt[prev]);
   bool run = (gid >= __ldcg(&ctl->first_gate)) && (__ldcg(&ctl->stall) == 0u) &&
              (__ldcg(&ctl->error) == 0u);
-  const bool room = 2ull * T0 <= t.cap;
+  const bool room = gate_fits(t, T0);
   if (threadIdx.x == 0) {
     if (blockIdx.x == 0 && run && !room) ctl->stall = gid + 1;  // every block skips
     if (blockIdx.x == 0 && run && room) {
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : ((W == 1) ? 4 : 2))
       if (gid + 1 < n_gates) fetch_args(gid + 1, buf ^ 1);
       continue;
     }
-    if (2ull * T0 > t.cap) {  // the same decision in every block
+    if (!gate_fits(t, T0)) {  // the same decision in every block
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->stall = gid + 1;
       end = gid;
       break;

@@ -125,7 +125,7 @@ extern "C" pp_status pp_merge_terms_noalloc(int n_qubits, int symmetry, int64_t 
   clear_scratch_kernel<<<sms, kBlock, 0, s>>>(index, slots, ctl);
   e = cudaGetLastError();
   if (e == cudaSuccess && m > 0) {
-    DevTable dst;
+    DevTable dst = {};
     dst.keys = keys_out;
     dst.coef = coef_out;
     dst.index = reinterpret_cast<uint64_t*>(index);

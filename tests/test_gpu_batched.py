@@ -53,7 +53,9 @@ def run_batched(n, B, steps, eps, wmax, group, f32, seed=0, state=None, noise_p=
 
 
 def rows_dict(x, z, c):
-    return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): c[i] for i in range(len(c))}
+    d = {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): c[i] for i in range(len(c))}
+    assert len(d) == len(c), "a string appears twice in the table"
+    return d
 
 
 @pytest.mark.parametrize("n,B,eps,wmax", [(10, 5, 1e-4, 6), (12, 33, 0.0, 5), (64, 8, 1e-3, 4)])

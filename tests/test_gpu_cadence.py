@@ -24,8 +24,10 @@ def _built():
 
 
 def as_dict(x, z, c):
-    return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
-            for i in range(len(c))}
+    d = {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
+        for i in range(len(c))}
+    assert len(d) == len(c), "a string appears twice in the table"
+    return d
 
 
 def run_schedule(wl, group, every, merge_method=pp.MERGE_HASH):

@@ -34,8 +34,10 @@ def _no_injection():
 
 
 def as_dict(x, z, c):
-    return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
-            for i in range(len(c))}
+    d = {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
+        for i in range(len(c))}
+    assert len(d) == len(c), "a string appears twice in the table"
+    return d
 
 
 def oracle_after(wl, layers):

@@ -31,8 +31,10 @@ def _built():
 def as_dict(x, z, c):
     x = np.asarray(x).reshape(len(c), -1)
     z = np.asarray(z).reshape(len(c), -1)
-    return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
-            for i in range(len(c))}
+    d = {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): float(c[i])
+        for i in range(len(c))}
+    assert len(d) == len(c), "a string appears twice in the table"
+    return d
 
 
 def rand_strings(n, m, seed, pool=None):

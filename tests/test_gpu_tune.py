@@ -24,7 +24,9 @@ def as_dict(x, z, c):
         return {}
     x = np.asarray(x).reshape(len(c), -1)
     z = np.asarray(z).reshape(len(c), -1)
-    return {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): c[i] for i in range(len(c))}
+    d = {tuple(int(v) for v in x[i]) + tuple(int(v) for v in z[i]): c[i] for i in range(len(c))}
+    assert len(d) == len(c), "a string appears twice in the table"
+    return d
 
 
 def layers(wl):
