@@ -636,14 +636,30 @@ def bench_workload(args):
             line("ring64_256_columns_one_at_a_time_3steps", total_ms, total_upd,
                  {"unit_note": "column updates; each column truncated on its own"})
     if "canon64" in names:
-        # representatives of 2^24 random n=64 strings (16 B each), resident in HBM:
-        # 512 MB read + written per call, far above L2
-        m, n = 1 << 24, 64
-        rng = np.random.default_rng(3)
-        keys = torch.from_numpy(rng.integers(0, 2 ** 63, size=(m, 2), dtype=np.int64)).cuda()
-        out = torch.empty_like(keys)
+        # representatives of 2^24 random n=64 strings (16 B each) and 2^23
+        # random n=128 strings (32 B each), resident in HBM: 512 MB read +
+        # written per call, far above L2
         hbm, kind = peaks()
-        for label, code in (("Z64", pp.SYM_ZN), ("D64", pp.SYM_DN), ("S64", pp.SYM_SN)):
+        rng = np.random.default_rng(3)
+        cases = []
+        for m, n in ((1 << 24, 64), (1 << 23, 128)):
+            W = n // 64
+            keys = torch.from_numpy(rng.integers(0, 2 ** 63, size=(m, 2 * W), dtype=np.int64)).cuda()
+            for label, code in (("Z", pp.SYM_ZN), ("D", pp.SYM_DN), ("S", pp.SYM_SN)):
+                cases.append((m, n, keys, "%s%d" % (label, n), code))
+        # 2^22 strings of weight <= 10 on 64 qubits, the shape of propagated
+        # tables (mostly I): the Z_n search walks the gaps between their sites
+        m = 1 << 22
+        sites = rng.integers(0, 64, size=(m, 10))
+        letters = rng.integers(0, 4, size=(m, 10))  # 0 leaves the site as I
+        bit = np.left_shift(np.uint64(1), sites.astype(np.uint64))
+        xw = np.bitwise_or.reduce(np.where((letters == 1) | (letters == 2), bit, np.uint64(0)), axis=1)
+        zw = np.bitwise_or.reduce(np.where((letters == 2) | (letters == 3), bit, np.uint64(0)), axis=1)
+        keys = torch.from_numpy(np.stack([xw, zw], axis=1).view(np.int64)).cuda()
+        for label, code in (("Z", pp.SYM_ZN), ("S", pp.SYM_SN)):
+            cases.append((m, 64, keys, "%s64w10" % label, code))
+        for m, n, keys, label, code in cases:
+            out = torch.empty_like(keys)
             pp.pp_canonical_keys(n, code, m, keys, out)
             torch.cuda.synchronize()
             t0 = torch.cuda.Event(enable_timing=True)
@@ -654,11 +670,12 @@ def bench_workload(args):
             t1.record()
             torch.cuda.synchronize()
             ms = t0.elapsed_time(t1) / 5
-            gbs = 2 * 16 * m / (ms / 1e3) / 1e9
+            gbs = 2 * 16 * (n // 64) * m / (ms / 1e3) / 1e9
             print(json.dumps({"metric": "canonical_keys_per_s", "value": m / (ms / 1e3),
                               "unit": "keys/s", "n_gpus": 1, "ms_per_call": ms,
                               "higher_is_better": True, "data": "synthetic",
-                              "config": {"workload": "canonical_keys_n64_%s_16M" % label},
+                              "config": {"workload": "canonical_keys_n%d_%s_%dM"
+                                         % (n, label, m >> 20)},
                               "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
                                       "peak_kind": kind}}), flush=True)
     if "merge32" in names:

@@ -371,6 +371,15 @@ __device__ __forceinline__ Mask<W> mask_rot(const Mask<W>& v, int j, int n, cons
   }
 }
 
+// More than one bit set.
+template <int W>
+__device__ __forceinline__ bool mask_many(const Mask<W>& v) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) c += __popcll(v.w[i]);
+  return c > 1;
+}
+
 template <int W>
 __device__ __forceinline__ bool mask_any(const Mask<W>& v) {
   uint64_t a = 0;
@@ -401,17 +410,46 @@ __device__ __forceinline__ Key<W> rotate_key(const Key<W>& k, int j, int n, cons
 template <int W>
 __device__ __forceinline__ bool key_less(const Key<W>& a, const Key<W>& b);
 
+// Set bit s of a W-word mask (compile-time word indices only).
+template <int W>
+__device__ __forceinline__ void mask_set(Mask<W>& m, int s) {
+#pragma unroll
+  for (int t = 0; t < W; ++t) m.w[t] |= (t == (s >> 6)) ? (1ull << (s & 63)) : 0ull;
+}
+
+// Strings with at most this many sites that differ from the smallest digit
+// find their longest runs by walking the gaps between those sites.
+constexpr int kZnGapWalk = 12;
+
+// A run of `gap` d's ends just before site s: keep s if the run is the
+// longest so far (L), alone if it is longer than all before.
+template <int W>
+__device__ __forceinline__ void zn_take_gap(Mask<W>& cand, int& L, int gap, int s) {
+  if (gap > L) {
+    L = gap;
+#pragma unroll
+    for (int i = 0; i < W; ++i) cand.w[i] = 0;
+  }
+  if (gap == L) mask_set<W>(cand, s);
+}
+
 // Z_n (Algorithm 2): the translation with the lowest digit integer.  Instead
 // of comparing all n translations, the search keeps only those that can be
 // lowest: the top digit of the lowest one is the smallest digit d present,
 // and the longer the run of d at the top, the lower the integer (a shorter
 // run is followed by a larger digit).  So the candidates put a longest
-// cyclic run of d on qubits n-L..n-1.  Bit p of M_L marks a window
-// p..p+L-1 (cyclic) of d's; M_{2^k} comes from doubling
-// (M_{2a} = M_a & T^a M_a) and the longest L from binary lifting over those,
-// in O(log n) mask operations.  The (usually one) candidates are then
-// compared as digit integers.  Equal to the exhaustive search by
-// construction; tested bit for bit against the oracle's enumeration.
+// cyclic run of d on the top qubits n-L..n-1, that is, translate by j where
+// j is the site just after the run.  The runs are found in one of two ways,
+// both giving every longest run:
+//  * few sites differ from d (a low-weight string, d = I): walk the gaps
+//    between consecutive such sites, cyclically; a gap before site s is a
+//    run ending just before s, so j = s;
+//  * otherwise (runs are short): shrink the mask of d's, cur &= T cur, until
+//    one more step would empty it; after L-1 steps bit p marks a window
+//    p..p+L-1 of d's, and j = p + L mod n.
+// The (usually one) candidates are then narrowed digit by digit on masks.
+// Equal to the exhaustive search by construction; tested bit for bit against
+// the oracle's enumeration.
 template <int W>
 __device__ __forceinline__ void canon_zn(Key<W>& k, int n) {
   const Mask<W> nm = nbits_mask<W>(n);
@@ -430,48 +468,90 @@ __device__ __forceinline__ void canon_zn(Key<W>& k, int n) {
     dm.w[i] = any_i ? (~sup.w[i] & nm.w[i])
                     : (any_x ? (k.x(i) & ~k.z(i)) : (any_y ? (k.x(i) & k.z(i)) : (k.z(i) & ~k.x(i))));
   }
-  constexpr int kMaxK = (W == 1) ? 6 : (W == 2 ? 7 : 8);  // 2^(kMaxK+1) > 64 W >= n
-  Mask<W> M[kMaxK + 1];
-  M[0] = dm;
-  int K = 0;
-#pragma unroll
-  for (int t = 0; t < kMaxK; ++t) {
-    if ((2 << t) <= n) {
-      const Mask<W> r = mask_rot<W>(M[t], 1 << t, n, nm);
-#pragma unroll
-      for (int i = 0; i < W; ++i) M[t + 1].w[i] = M[t].w[i] & r.w[i];
-      K = t + 1;
-    }
-  }
-  Mask<W> cur = nm;  // windows of length 0: every position
-  int L = 0;
-#pragma unroll
-  for (int t = kMaxK; t >= 0; --t) {
-    if (t <= K && L + (1 << t) <= n) {
-      const Mask<W> r = mask_rot<W>(M[t], L, n, nm);
-      Mask<W> c;
-#pragma unroll
-      for (int i = 0; i < W; ++i) c.w[i] = cur.w[i] & r.w[i];
-      if (mask_any<W>(c)) {
-        cur = c;
-        L += 1 << t;
-      }
-    }
-  }
-  if (L >= n) return;  // one letter everywhere: every translation is the same string
-  Key<W> best = k;
-  bool first = true;
+  Mask<W> E;  // sites that differ from d
+  int n_other = 0;
 #pragma unroll
   for (int i = 0; i < W; ++i) {
-    uint64_t m = cur.w[i];
+    E.w[i] = ~dm.w[i] & nm.w[i];
+    n_other += __popcll(E.w[i]);
+  }
+  if (n_other == 0) return;  // one letter everywhere: every translation is the same string
+  Mask<W> cand;
+#pragma unroll
+  for (int i = 0; i < W; ++i) cand.w[i] = 0;
+  int L = -1;  // length of the longest runs
+  if (n_other <= kZnGapWalk) {
+    int first = -1, prev = -1;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      uint64_t m = E.w[i];
+      while (m) {
+        const int s = 64 * i + __ffsll((long long)m) - 1;
+        m &= m - 1;
+        if (first < 0) first = s;
+        else zn_take_gap<W>(cand, L, s - prev - 1, s);
+        prev = s;
+      }
+    }
+    zn_take_gap<W>(cand, L, first + n - prev - 1, first);  // the run wrapping past qubit n-1
+  } else {
+    Mask<W> cur = dm;
+    L = 1;
+    for (;;) {
+      const Mask<W> r = mask_rot<W>(cur, 1, n, nm);
+      Mask<W> nx;
+#pragma unroll
+      for (int i = 0; i < W; ++i) nx.w[i] = cur.w[i] & r.w[i];
+      if (!mask_any<W>(nx)) break;
+      cur = nx;
+      ++L;
+    }
+    cand = mask_rot<W>(cur, n - L, n, nm);  // bit p of cur -> bit (p + L) mod n
+  }
+  // The candidates share the run on the top L qubits.  Below it, digit by
+  // digit from the top, keep the candidates with the smallest digit (high
+  // bit, then low bit of the digit), all candidates at once on masks; after
+  // kZnNarrow digits (or all n - L, when several left give the same string)
+  // any candidates still tied are compared as whole rotated strings.
+  constexpr int kZnNarrow = 2;
+  Mask<W> zp, lp;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    zp.w[i] = k.z(i);
+    lp.w[i] = k.x(i) ^ k.z(i);
+  }
+  for (int kk = 1; kk <= kZnNarrow && kk <= n - L && mask_many<W>(cand); ++kk) {
+    const int sft = n - L - kk;  // bit j of the rotation = the digit at j - L - kk
+    const Mask<W> hi = mask_rot<W>(zp, sft, n, nm);
+    Mask<W> c0;
+    bool any0 = false;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      c0.w[i] = cand.w[i] & ~hi.w[i];
+      any0 |= c0.w[i] != 0;
+    }
+    if (any0) cand = c0;
+    const Mask<W> lo = mask_rot<W>(lp, sft, n, nm);
+    Mask<W> c1;
+    bool any1 = false;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      c1.w[i] = cand.w[i] & ~lo.w[i];
+      any1 |= c1.w[i] != 0;
+    }
+    if (any1) cand = c1;
+  }
+  Key<W> best = k;
+  bool first_c = true;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    uint64_t m = cand.w[i];
     while (m) {
-      const int p = 64 * i + __ffsll((long long)m) - 1;
+      const int j = 64 * i + __ffsll((long long)m) - 1;
       m &= m - 1;
-      int j = p + L;
-      j -= (j >= n) ? n : 0;
       const Key<W> r = rotate_key<W>(k, j, n, nm);
-      if (first || key_less<W>(r, best)) best = r;
-      first = false;
+      if (first_c || key_less<W>(r, best)) best = r;
+      first_c = false;
     }
   }
   k = best;
@@ -530,12 +610,20 @@ __device__ __forceinline__ Key<W> reflect_key(const Key<W>& k, int n) {
     r.x(0) = __brevll(k.x(0)) >> (64 - n);
     r.z(0) = __brevll(k.z(0)) >> (64 - n);
   } else {
+    // reversing the word order and the bits of every word sends bit q to
+    // bit 64 W - 1 - q; a shift right by 64 W - n brings it to n - 1 - q
+    Mask<W> xm, zm;
 #pragma unroll
-    for (int j = 0; j < 2 * W; ++j) r.w[j] = 0;
-    for (int q = 0; q < n; ++q) {
-      const int t = n - 1 - q;
-      r.x(t >> 6) |= ((k.x(q >> 6) >> (q & 63)) & 1ull) << (t & 63);
-      r.z(t >> 6) |= ((k.z(q >> 6) >> (q & 63)) & 1ull) << (t & 63);
+    for (int j = 0; j < W; ++j) {
+      xm.w[j] = __brevll(k.x(W - 1 - j));
+      zm.w[j] = __brevll(k.z(W - 1 - j));
+    }
+    xm = mask_shr<W>(xm, 64 * W - n);
+    zm = mask_shr<W>(zm, 64 * W - n);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      r.x(j) = xm.w[j];
+      r.z(j) = zm.w[j];
     }
   }
   return r;
