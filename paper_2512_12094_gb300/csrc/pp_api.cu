@@ -134,6 +134,7 @@ struct pp_ctx {
   std::vector<double> sn_bloch;  // bloch vectors the S_n table was built for
   uint64_t n_terms = 0;          // host mirror of DevCtl::n_terms
   int64_t n_live = 0;
+  bool live_known = true;  // n_live equals the device's count (false after a kernel changed it unread)
   bool merged = true;
   bool obs_invariant = false;
   size_t bytes = 0;
@@ -384,6 +385,7 @@ pp_status ctl_commit(pp_ctx* c) {
   PP_TRY(check_device_error(c));
   c->n_terms = c->h_ctl->n_terms;
   c->n_live = c->h_ctl->n_live;
+  c->live_known = true;
   return PP_OK;
 }
 
@@ -403,7 +405,16 @@ pp_status compact_into(pp_ctx* c, int dst, double extra_eps, int extra_wmax) {
                            c->cfg.coeff_eps, extra_eps, extra_wmax, c->d_ctl));
   }
   c->launches += 1;
-  PP_TRY(ctl_commit(c));
+  if (extra_eps == 0.0 && extra_wmax < 0 && c->live_known) {
+    // A compaction without extra truncation keeps exactly the live entries,
+    // whose count the host already holds, so the control block is updated on
+    // the stream without a round trip (errors surface at the next read).
+    PP_CUDA(cudaMemcpyAsync(&c->d_ctl->n_terms, &c->d_ctl->n_next, 8, cudaMemcpyDeviceToDevice,
+                            c->stream));
+    c->n_terms = (uint64_t)std::max<int64_t>(c->n_live, 0);
+  } else {
+    PP_TRY(ctl_commit(c));
+  }
   PP_TRY(activate(c, dst));
   c->compactions++;
   return PP_OK;
@@ -570,6 +581,7 @@ pp_status queue_merge(pp_ctx* c, int group) {
 pp_status finish_queued_merge(pp_ctx* c) {
   c->n_terms = c->h_ctl->n_terms;
   c->n_live = c->h_ctl->n_live;
+  c->live_known = true;
   PP_TRY(activate(c, 1 - c->active));
   c->merged = true;
   c->merges++;
@@ -1229,6 +1241,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   if (c->cfg.noise_mode == PP_NOISE_PER_LAYER && c->n_terms > 0) {
     PP_CUDA(launch_damp_layer(c->W, grid_for(c, c->n_terms, 4), c->stream,
                               desc_of(c, c->buf[c->active]), c->d_ctl, c->d_ldamp, c->cfg.coeff_eps));
+    c->live_known = false;  // damping may truncate entries
     c->launches += 1;
   }
   // room for 2 x room_factor (1.25 unless configured) times the growth the
@@ -1314,6 +1327,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
         } else {
           c->n_terms = c->h_ctl->n_terms;
           c->n_live = c->h_ctl->n_live;
+          c->live_known = true;
         }
         break;
       }
@@ -1322,6 +1336,7 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
       c->stalls++;
       c->n_terms = c->h_ctl->n_terms;
       c->n_live = c->h_ctl->n_live;
+      c->live_known = true;
       PP_TRY(make_room(c, std::max<uint64_t>(factor, 4)));
       if (layered) grid_b = layered_grid(c->n_terms);
       first = end;
@@ -1768,6 +1783,7 @@ pp_status pp_num_terms(pp_ctx* c, int64_t* live, int64_t* stored) {
   PP_TRY(read_ctl(c));
   c->n_terms = c->h_ctl->n_terms;
   c->n_live = c->h_ctl->n_live;
+  c->live_known = true;
   if (live) *live = c->n_live;
   if (stored) *stored = (int64_t)c->n_terms;
   return PP_OK;
