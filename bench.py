@@ -519,6 +519,23 @@ def bench_serving(args):
             "offered_load_wall_s": float(specs[-1][0]),
             "max_abs_diff_vs_sequential": err}
     print(json.dumps(line), flush=True)
+    if args.serving_dump:
+        stream = pi.serving_stream(2000, args.rate, 0) if full else None
+        recs = []
+        for k, ((arrival, wl), r) in enumerate(zip(specs, res)):
+            rec = {"arrival_s": arrival, "n": wl.circuit.n, "layers": len(wl.circuit.layers),
+                   "gates_per_layer": len(wl.circuit.layers[0]), "eps": wl.eps,
+                   "group": wl.symmetry, "noise_mode": wl.noise_mode,
+                   "family": "a2a" if wl.noise_mode == 1 else "ring"}
+            if stream is not None:
+                rec["steps"] = stream[k]["steps"]
+            rec.update({key: r[key] for key in ("status", "latency_ms", "queue_ms", "run_ms",
+                                                "grows", "restarts", "reserved_bytes",
+                                                "device_bytes", "live_terms", "gate_updates")
+                        if key in r})
+            recs.append(rec)
+        with open(args.serving_dump, "w") as f:
+            json.dump(recs, f)
 
 
 def replica_throughput(dist, ms_total, e2e_ms, upd, device):
@@ -850,6 +867,9 @@ def main():
                     help="serve the first N jobs of the 2000-job stream at their stated sizes")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serving-dump", default="",
+                    help="with --serving/--serving-full: write every job's description and "
+                         "result to this JSON file")
     ap.add_argument("--workload", default="",
                     help="comma list of a2a64, batched64, columns64, xxz36, canon64, merge32, "
                          "rows64, cadence: time those")

@@ -147,7 +147,7 @@ struct pp_ctx {
   double last_growth = 2.0;  // stored entries after / before the gates of the last layer
   double grid_scale = 1.0;   // blocks per launch relative to the default sizing (pp_tune)
   double index_factor = 1.5; // hash index slots per table entry of capacity (pp_tune)
-  int grid_share = 1;        // a persistent layer launch takes at most 1/grid_share of the GPU
+  double grid_frac = 1.0;    // a persistent layer launch takes at most this fraction of the GPU
   double gate_ms = 0.0;
   int64_t gates_timed = 0;
   void* sort_scratch = nullptr;  // scratch of the sort-based merge (merge_method 1)
@@ -1234,6 +1234,20 @@ pp_status restore_snapshot(pp_ctx* c, const Buf& s, uint64_t n) {
   return PP_OK;
 }
 
+// Blocks a persistent layer launch over a table of n_now stored strings asks
+// for: one string per thread per pass (batched rows B/32 times as many, and
+// sized for the table the layer is expected to reach), times the tuner's grid
+// scale; never more than the GPU holds at once.
+uint64_t layer_grid_want(const pp_ctx* c, uint64_t n_now) {
+  const int nt = c->batched ? kBlock : c->layer_threads;
+  const uint64_t rowf = c->batched ? std::max<uint64_t>(1, (uint64_t)c->B / 32) : 1;
+  const double grow = c->batched ? std::max(1.25, c->last_growth) : 1.25;
+  const double e = std::max(1.0, (double)n_now * grow);
+  const uint64_t want = (uint64_t)std::ceil(e * (double)rowf * c->grid_scale / nt);
+  const uint64_t full = std::max<uint64_t>(1, (uint64_t)c->sms * c->layer_bps);
+  return std::min<uint64_t>(std::max<uint64_t>(want, 1), full);
+}
+
 // Everything pp_apply_layer does after the entry merge: damping, room, the
 // gate launches (with the capacity-stall loop) and the boundary merge.
 pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::vector<int>& src_t,
@@ -1264,12 +1278,10 @@ pp_status apply_layer_core(pp_ctx* c, std::vector<GateArgs>& args, const std::ve
   // grows tenfold within the layer would otherwise run on a tenth of the
   // blocks; a relaunch after a stall sizes it again.
   auto layered_grid = [&](uint64_t n_now) {
-    const int nt = c->batched ? kBlock : c->layer_threads;
-    const double grow = c->batched ? std::max(1.25, c->last_growth) : 1.25;
-    const double e = std::max(1.0, (double)n_now * grow);
-    const uint64_t want = (uint64_t)std::ceil(e * (double)rowf * c->grid_scale / nt);
-    const uint64_t room = std::max<uint64_t>(1, (uint64_t)c->sms * c->layer_bps / c->grid_share);
-    return (int)std::min<uint64_t>(std::max<uint64_t>(want, 1), room);
+    const uint64_t want = layer_grid_want(c, n_now);
+    const uint64_t room = std::max<uint64_t>(
+        1, (uint64_t)std::floor((double)c->sms * c->layer_bps * c->grid_frac));
+    return (int)std::min<uint64_t>(want, room);
   };
   if (layered) {
     grid_b = layered_grid(c->n_terms);
@@ -2037,6 +2049,12 @@ pp_status pp_overlap_sum(int n_qubits, int symmetry, int64_t m, const uint64_t* 
 
 bool ppk::valid_group_code(int code, int n) { return valid_group(code, n); }
 
-void ppk::set_grid_share(pp_ctx* c, int parts) {
-  if (c) c->grid_share = std::max(1, parts);
+void ppk::set_grid_fraction(pp_ctx* c, double frac) {
+  if (c) c->grid_frac = std::min(1.0, std::max(frac, 1e-9));
+}
+
+double ppk::layer_fraction_wanted(const pp_ctx* c) {
+  if (!c || !c->cfg.layer_kernel || c->layer_bps <= 0) return 0.0;
+  const double full = (double)c->sms * c->layer_bps;
+  return std::min(1.0, (double)layer_grid_want(c, c->n_terms) / full);
 }

@@ -222,10 +222,13 @@ bool valid_group_code(int code, int n);
 }  // namespace ppk
 struct pp_ctx;
 namespace ppk {
-// Limit a context's persistent layer launches to 1/parts of the GPU's
-// co-resident blocks, so that `parts` contexts running at once (the server's
-// jobs) can overlap.
-void set_grid_share(pp_ctx* c, int parts);
+// Limit a context's persistent layer launches to the fraction `frac` (0, 1]
+// of the GPU's co-resident blocks, so that contexts whose fractions add up to
+// at most 1 (the server's jobs) can run their layers at the same time.
+void set_grid_fraction(pp_ctx* c, double frac);
+// The fraction of the GPU's co-resident blocks the context's next persistent
+// layer launch would use with no limit (0 when it has no persistent path).
+double layer_fraction_wanted(const pp_ctx* c);
 
 // ------------------------------------------------------- batched launchers
 // Same contracts as the single-column kernels above, on B-column rows.

@@ -7,8 +7,9 @@
 // arrives while others run starts as soon as a slot and memory are free, and
 // the kernels of different jobs overlap on the device.  A job runs in its own
 // context (tables resident on the device for its whole life) whose memory
-// budget is its reservation; its layers run as persistent launches on at most
-// 1/slots of the GPU.
+// budget is its reservation; each of its layers runs as one persistent launch
+// on the share of the GPU's co-resident blocks it holds for that layer
+// (an equal share among the running jobs, at least 1/slots).
 //
 // Reservations follow the jobs' live-term counts.  A job's first reservation
 // is the memory of a table for its observable (unless the job names one).
@@ -87,6 +88,7 @@ struct pp_server {
   std::deque<std::unique_ptr<Job>> queue;
   std::map<uint64_t, Done> results;
   int64_t running = 0, completed = 0;
+  int units_free = 0;  // share units of the GPU's co-resident blocks not held by a layer
   std::mutex mu;
   std::condition_variable cv_work;  // workers: a job or memory became available
   std::condition_variable cv_done;  // waiters: a job finished
@@ -97,6 +99,11 @@ namespace {
 
 constexpr int kMaxBypass = 8;
 constexpr size_t kMiB = (size_t)1 << 20;
+// The GPU's co-resident blocks, in share units handed to the layers of
+// running jobs: a job's persistent layer launch holds its units while it
+// runs, and the units held at any time add up to at most the whole GPU, so
+// the cooperative launches of all jobs fit at once.
+constexpr int kShareUnits = 1024;
 
 size_t round_mib(double b) { return ((size_t)std::ceil(b / (double)kMiB) + 1) * kMiB; }
 
@@ -128,6 +135,39 @@ std::unique_ptr<Job> take_fitting(pp_server* s) {
     if ((*it)->bypassed >= kMaxBypass) return nullptr;
   }
   return nullptr;
+}
+
+// Share units for one layer of a job whose launch would use the fraction
+// `wanted` of the GPU.  Every layer gets 1/slots of the GPU, as a fixed split
+// would give it (a table may grow far beyond its size at the layer's start
+// and relaunch on more blocks after a stall).  A job that can use more gets
+// up to an equal share among the running jobs.  A queued job that fits in
+// memory is admitted as soon as a slot is free, so fewer running jobs than
+// slots means the others wait for memory: then a few large jobs, or one at
+// the end of a stream, get the GPU instead of leaving it idle.  Waits until
+// 1/slots is free; units come back at the end of every layer, so the wait
+// ends.
+int acquire_units(pp_server* s, double wanted) {
+  std::unique_lock<std::mutex> lock(s->mu);
+  const int floor_units = std::max(1, kShareUnits / s->slots);
+  for (;;) {
+    const int fair =
+        std::max(floor_units, kShareUnits / (int)std::max<int64_t>(1, s->running));
+    const int want =
+        std::max(floor_units, std::min(fair, (int)std::ceil(wanted * kShareUnits)));
+    if (s->units_free >= floor_units) {
+      const int take = std::min(want, s->units_free);
+      s->units_free -= take;
+      return take;
+    }
+    s->cv_work.wait(lock);
+  }
+}
+
+void release_units(pp_server* s, int units) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->units_free += units;
+  s->cv_work.notify_all();
 }
 
 enum class Grow { kGranted, kNever, kGiveBack };
@@ -185,10 +225,6 @@ pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, b
                    j.coef.data(), &ctx);
     if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
   }
-  // A job's layers run in one persistent launch each, on at most its share of
-  // the GPU, so that the jobs of all slots overlap; a small table runs in a
-  // single block with no grid barrier at all.
-  if (st == PP_OK) ppk::set_grid_share(ctx, s->slots);
   int64_t live_prev = -1;
   for (int l = 0; st == PP_OK && l < j.n_layers; ++l) {
     // proactive: the memory the context holds, scaled by the live-term
@@ -210,7 +246,15 @@ pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, b
       }
     }
     for (;;) {
+      // A layer runs in one persistent launch on the share units it holds
+      // (a job running alone gets the whole GPU); the units go back before
+      // any wait for memory, so no job waits for memory while holding units
+      // another job needs in order to finish.
+      const double wanted = ppk::layer_fraction_wanted(ctx);
+      const int units = wanted > 0.0 ? acquire_units(s, wanted) : 0;
+      if (units > 0) ppk::set_grid_fraction(ctx, (double)units / kShareUnits);
       st = pp_apply_layer(ctx, (int)j.gates.size(), j.gates.data(), j.theta.data(), j.boundary);
+      if (units > 0) release_units(s, units);
       if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
     }
   }
@@ -295,6 +339,7 @@ pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_jo
   s->budget = mem_budget_bytes;
   s->slots = slots;
   s->default_reserve = default_job_bytes;  // 0: each job's reservation is estimated
+  s->units_free = kShareUnits;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     ppk::set_last_error("pp_server_create: no CUDA device");
