@@ -156,6 +156,69 @@ def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, o
     return vals, stats
 
 
+def run_job_concurrent(pp, wl, layers, obs_dev, streams, join, host_inputs, plain_share,
+                       block_threads=0):
+    """One job with its two propagations (plain and Z_n-merged) at the same
+    time, each driven by its own host thread on its own stream.  The plain
+    run's persistent layer launches take the fraction plain_share of the GPU
+    and the merged run's the rest (pp_set_grid_fraction), so both fit at once;
+    when the plain run's last layer has returned, the merged run takes the
+    whole GPU from its next layer on.  Returns (vals, stats, start, ends, end):
+    CUDA events on the joining stream (start, end) and each run's own end."""
+    import threading
+    import torch
+    n = wl.circuit.n
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    start.record(join)
+    for s_ in streams:
+        s_.wait_event(start)
+    vals, stats, errors = [None, None], [None, None], []
+    plain_done = threading.Event()
+
+    def run(gi):
+        try:
+            stream = streams[gi]
+            cfg = pp.pp_config_default(n_qubits=n, symmetry=gi, coeff_eps=wl.eps,
+                                       max_weight=wl.max_weight, cuda_stream=stream,
+                                       block_threads=block_threads)
+            if host_inputs:
+                ox, oz, oc = wl.observable.arrays()
+                ctx = pp.pp_create(cfg, ox, oz, oc)
+            else:
+                dx, dz, dc = obs_dev
+                ctx = pp.pp_create_device(cfg, len(wl.observable.terms), dx, dz, dc)
+            share = plain_share if gi == 0 else 1.0 - plain_share
+            pp.pp_set_grid_fraction(ctx, share)
+            for packed, th in layers:
+                if gi == 1 and share < 1.0 and plain_done.is_set():
+                    share = 1.0  # the plain run's layer launches are all finished
+                    pp.pp_set_grid_fraction(ctx, share)
+                pp.pp_apply_layer(ctx, packed, th, True)
+            if gi == 0:
+                plain_done.set()
+            vals[gi] = pp.pp_expect(ctx, wl.state.bloch)
+            stats[gi] = pp.pp_stats(ctx)
+            pp.pp_destroy(ctx)
+            ends[gi].record(stream)
+        except Exception as e:  # noqa: BLE001 - re-raised below
+            plain_done.set()
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(gi,)) for gi in (0, 1)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    for e in ends:
+        join.wait_event(e)
+    end.record(join)
+    return vals, stats, start, ends, end
+
+
 def bench_ours(args):
     import torch
     import paper_2512_12094_gb300 as pp
@@ -189,21 +252,32 @@ def bench_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    concurrent = args.only == "both" and args.plain_share > 0.0
+    job_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+
     def timed_job(host_inputs, profile):
+        """(vals, stats, total ms, [plain ms, merged ms]); the two propagations
+        run at the same time unless profiling or --plain-share 0."""
         flush.zero_()
         barrier()
+        if concurrent and not profile:
+            vals, stats, start, ends, end = run_job_concurrent(
+                pp, wl, layers, obs_dev, job_streams, stream, host_inputs, args.plain_share,
+                block_threads=args.block_threads)
+            end.synchronize()
+            return vals, stats, start.elapsed_time(end), [start.elapsed_time(e) for e in ends]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         if args.only != "both":
             ev[1] = ev[0]
         vals, stats = run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=ev,
                               only=args.only, block_threads=args.block_threads)
         ev[2].synchronize()
-        return vals, stats, ev
+        return vals, stats, ev[0].elapsed_time(ev[2]), [ev[0].elapsed_time(ev[1]),
+                                                         ev[1].elapsed_time(ev[2])]
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            run_job(pp, wl, layers, obs_dev, stream, False, False, only=args.only,
-                    block_threads=args.block_threads)
+            timed_job(False, False)
         barrier()
         clocks = ClockSampler(local)
         clocks.start()
@@ -212,11 +286,11 @@ def bench_ours(args):
         vals = stats = None
         for _ in range(args.steps):
             # no per-kernel events here: the job exactly as a user runs it
-            vals, stats, ev = timed_job(False, False)
-            ms_total += ev[0].elapsed_time(ev[2])
+            vals, stats, ms, parts = timed_job(False, False)
+            ms_total += ms
             if args.only == "both":
-                split[0] += ev[0].elapsed_time(ev[1])
-                split[1] += ev[1].elapsed_time(ev[2])
+                split[0] += parts[0]
+                split[1] += parts[1]
             for st in stats:
                 upd += st["gate_updates"]
                 launches += st["kernel_launches"]
@@ -225,8 +299,8 @@ def bench_ours(args):
         e2e_ms = 0.0
         if not args.no_e2e:
             for _ in range(args.steps):
-                _, _, ev = timed_job(True, False)
-                e2e_ms += ev[0].elapsed_time(ev[2])
+                _, _, ms, _ = timed_job(True, False)
+                e2e_ms += ms
         clk = clocks.stop()  # both timed regions
         barrier()
         # roofline pass: the same jobs with CUDA events around every layer kernel
@@ -234,7 +308,7 @@ def bench_ours(args):
         pupd = ac = gate_ms = skipped = 0.0
         gate_n = gates_skipped = 0
         for _ in range(args.steps):
-            _, pstats, _ = timed_job(False, True)
+            _, pstats, _, _ = timed_job(False, True)
             for st in pstats:
                 pupd += st["gate_updates"]
                 skipped += st["skipped_updates"]
@@ -272,6 +346,10 @@ def bench_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "breakdown_ms_per_step": {"plain": split[0] / args.steps, "zn": split[1] / args.steps,
                                   "layer_kernels_instrumented_pass": gate_ms / args.steps},
+        "schedule": ({"propagations": "plain and Z_32 at the same time, one host thread and "
+                                      "stream each; breakdown = each run's own span",
+                      "plain_grid_fraction": args.plain_share}
+                     if concurrent else {"propagations": "plain, then Z_32, on one stream"}),
         "result": result_summary(vals, stats, args.only),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -859,6 +937,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--plain-share", type=float, default=0.25,
+                    help="run the plain and Z_32 propagations of a job at the same time, the "
+                         "plain one on this fraction of the GPU's co-resident blocks (0: one "
+                         "after the other)")
     ap.add_argument("--block-threads", type=int, default=0, choices=[0, 256, 1024],
                     help="block size of the persistent layer kernel (0: the library default)")
     ap.add_argument("--serving", type=int, default=0,

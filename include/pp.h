@@ -288,6 +288,16 @@ pp_status pp_stats(pp_ctx* ctx, pp_stats_t* out);
 /* Raise or lower the memory budget of a context (0 = no ceiling). */
 pp_status pp_set_budget(pp_ctx* ctx, size_t mem_budget_bytes);
 
+/* Limit the context's persistent layer launches (one cooperative launch per
+ * layer whose blocks wait for one another at a barrier between gates) to the
+ * fraction `fraction` in (0, 1] of the blocks the GPU holds at once (default
+ * 1).  Contexts driven from different host threads may apply layers at the
+ * same time only if the fractions of those running together add up to at
+ * most 1: then every launch fits beside the others.  A launch over a small
+ * table uses fewer blocks than its fraction allows.  Takes effect at the
+ * context's next layer.  PP_ERR_ARG for a fraction outside (0, 1]. */
+pp_status pp_set_grid_fraction(pp_ctx* ctx, double fraction);
+
 /* Wait for all work queued by ctx. */
 pp_status pp_synchronize(pp_ctx* ctx);
 

@@ -158,6 +158,7 @@ _SIGS = {
     "pp_export": [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64p],
     "pp_stats": [_vp, ctypes.POINTER(pp_stats_t)],
     "pp_set_budget": [_vp, ctypes.c_size_t],
+    "pp_set_grid_fraction": [_vp, ctypes.c_double],
     "pp_synchronize": [_vp],
     "pp_last_error": [],
     "pp_debug_fail_alloc_after": [ctypes.c_int64],
@@ -346,6 +347,10 @@ def pp_stats(ctx) -> dict:
 
 def pp_set_budget(ctx, nbytes: int):
     _check(load().pp_set_budget(ctx, int(nbytes)))
+
+
+def pp_set_grid_fraction(ctx, fraction: float):
+    _check(load().pp_set_grid_fraction(ctx, float(fraction)))
 
 
 def pp_synchronize(ctx):

@@ -1889,6 +1889,13 @@ pp_status pp_stats(pp_ctx* c, pp_stats_t* out) {
   return PP_OK;
 }
 
+pp_status pp_set_grid_fraction(pp_ctx* c, double fraction) {
+  if (!c) return fail(PP_ERR_ARG, "ctx is null");
+  if (!(fraction > 0.0 && fraction <= 1.0)) return fail(PP_ERR_ARG, "fraction must be in (0, 1]");
+  ppk::set_grid_fraction(c, fraction);
+  return PP_OK;
+}
+
 pp_status pp_set_budget(pp_ctx* c, size_t mem_budget_bytes) {
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   c->cfg.mem_budget_bytes = mem_budget_bytes;
