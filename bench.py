@@ -43,7 +43,7 @@ COEF_BYTES = 8   # FP64
 # of the Z_32-merged job, taken with the kernel sources whose digest is
 # recorded beside it.  When the sources differ from that digest the figure no
 # longer describes the kernel and the JSON line reports traffic as null.
-TRAFFIC_CAPTURE = {"ratio": 1.830, "sources_sha16": "97da5ada6879b7ac"}  # 7.956 GB / 4.346 GB
+TRAFFIC_CAPTURE = {"ratio": 2.595, "sources_sha16": "97da5ada6879b7ac"}  # 7.956 GB / 3.066 GB
 KERNEL_SOURCES = ["paper_2512_12094_gb300/csrc/pp_kernels.cu",
                   "paper_2512_12094_gb300/csrc/pp_device.cuh",
                   "paper_2512_12094_gb300/csrc/pp_internal.h"]
@@ -154,6 +154,58 @@ def run_job(pp, wl, layers, obs_dev, stream, host_inputs, profile, marks=None, o
     if marks is not None:
         marks[2].record(stream)
     return vals, stats
+
+
+def trace_layers(args):
+    """One JSON line per layer of the config-1 job (plain, then Z_32): live and
+    stored terms after the layer, the layer's gate updates and anticommuting
+    strings, the layer kernels' time (CUDA events around each launch) and the
+    whole layer's time (events around pp_apply_layer, merge included), and the
+    layer kernels' algorithmic bandwidth against the measured copy peak."""
+    import torch
+    import paper_2512_12094_gb300 as pp
+    torch.cuda.set_device(0)
+    pp.build()
+    pp.load()
+    wl = pi.config1_ring()
+    layers = []
+    for layer in reversed(range(len(wl.circuit.layers))):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        layers.append((pp.pack_gates(gx, gz), th))
+    ox, oz, oc = wl.observable.arrays()
+    hbm, kind = peaks()
+    stream = torch.cuda.Stream()
+    per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
+    with torch.cuda.stream(stream):
+        for label, group in (("plain", 0), ("Z32", 1)):
+            cfg = pp.pp_config_default(n_qubits=32, symmetry=group, coeff_eps=wl.eps,
+                                       max_weight=wl.max_weight, cuda_stream=stream,
+                                       profile_kernels=1)
+            ctx = pp.pp_create(cfg, ox, oz, oc)
+            prev = pp.pp_stats(ctx)
+            for k, (packed, th) in enumerate(layers):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pp.pp_apply_layer(ctx, packed, th, True)
+                e1.record(stream)
+                e1.synchronize()
+                st = pp.pp_stats(ctx)
+                upd = st["gate_updates"] - prev["gate_updates"]
+                skip = st["skipped_updates"] - prev["skipped_updates"]
+                ac = st["anticommuting_terms"] - prev["anticommuting_terms"]
+                kms = st["gate_kernel_ms"] - prev["gate_kernel_ms"]
+                alg = KEY_BYTES * (upd - skip) + per_ac * ac
+                gbs = alg / (kms / 1e3) / 1e9 if kms > 0 else None
+                print(json.dumps({"job": label, "layer": k, "live_terms": st["live_terms"],
+                                  "stored_terms": st["stored_terms"], "gate_updates": upd,
+                                  "skipped_updates": skip, "anticommuting_terms": ac,
+                                  "layer_kernel_ms": kms, "layer_ms": e0.elapsed_time(e1),
+                                  "algorithmic_gbs": gbs,
+                                  "frac": (gbs / hbm) if gbs else None, "peak_kind": kind,
+                                  "stalls": st["stalls"] - prev["stalls"]}), flush=True)
+                prev = st
+            pp.pp_destroy(ctx)
 
 
 def run_job_concurrent(pp, wl, layers, obs_dev, streams, join, host_inputs, plain_share,
@@ -457,10 +509,13 @@ def profile_layer(args):
             torch.cuda.profiler.stop()
             after = pp.pp_stats(ctx)
             upd = after["gate_updates"] - before["gate_updates"]
+            skip = after["skipped_updates"] - before["skipped_updates"]
             ac = after["anticommuting_terms"] - before["anticommuting_terms"]
             per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
-            print(json.dumps({"profile_layer": k, "updates": upd, "anticommuting_terms": ac,
-                              "algorithmic_bytes": KEY_BYTES * upd + per_ac * ac,
+            # the roofline's model: updates in gates the occupancy test skipped move no bytes
+            print(json.dumps({"profile_layer": k, "updates": upd, "skipped_updates": skip,
+                              "anticommuting_terms": ac,
+                              "algorithmic_bytes": KEY_BYTES * (upd - skip) + per_ac * ac,
                               "layer_kernel_ms": after["gate_kernel_ms"] - before["gate_kernel_ms"],
                               "launches": after["gate_kernels_timed"] - before["gate_kernels_timed"],
                               "live_terms": after["live_terms"]}), flush=True)
@@ -937,6 +992,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
+    ap.add_argument("--trace-layers", action="store_true",
+                    help="one JSON line per layer of the config-1 job (no timing contract)")
     ap.add_argument("--plain-share", type=float, default=0.25,
                     help="run the plain and Z_32 propagations of a job at the same time, the "
                          "plain one on this fraction of the GPU's co-resident blocks (0: one "
@@ -964,6 +1021,8 @@ def main():
         bench_serving(args)
     elif args.profile_layer >= 0:
         profile_layer(args)
+    elif args.trace_layers:
+        trace_layers(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

@@ -10,6 +10,7 @@
 // nothing and raises `stall`; the host then grows the tables and relaunches
 // the layer from that gate (earlier gates skip themselves).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -27,6 +28,15 @@
 using namespace ppk;
 
 namespace {
+
+// A named range on the host timeline for profilers (NVTX); costs nothing
+// when no tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 thread_local std::string g_last_error;
 
@@ -392,6 +402,7 @@ pp_status ctl_commit(pp_ctx* c) {
 // Copy the kept entries of the active table into `dst` (fresh index) and make
 // it active.  extra_eps / extra_wmax implement pp_truncate.
 pp_status compact_into(pp_ctx* c, int dst, double extra_eps, int extra_wmax) {
+  Range range_("compact");
   Buf& d = c->buf[dst];
   PP_CUDA(cudaMemsetAsync(d.index, 0, (size_t)d.icap * 8, c->stream));
   PP_TRY(ctl_prepare_insert(c, 0));
@@ -506,6 +517,7 @@ bool sort_merge_ready(pp_ctx* c, uint64_t count) {
 // Accumulate the active table (after optional canonicalisation) into the
 // spare table and make it active: the merge of Algorithms 2 and 3.
 pp_status merge_active(pp_ctx* c, int group) {
+  Range range_("merge");
   int dst = 1 - c->active;
   Buf& d = c->buf[dst];
   Buf& s = c->buf[c->active];
@@ -554,6 +566,7 @@ pp_status merge_active(pp_ctx* c, int group) {
 // reads the control block once afterwards (finish_queued_merge) instead of
 // once after the gates and once after the merge.
 pp_status queue_merge(pp_ctx* c, int group) {
+  Range range_("queue merge");
   const int dst = 1 - c->active;
   Buf& d = c->buf[dst];
   Buf& s = c->buf[c->active];
@@ -1394,16 +1407,19 @@ pp_status pp_debug_fail_alloc_after(int64_t n) {
 
 pp_status pp_create(const pp_config* cfg, int64_t n_terms, const uint64_t* x, const uint64_t* z,
                     const double* coef, pp_ctx** out) {
+  Range range_("pp_create");
   return create_common(cfg, n_terms, x, z, coef, false, out);
 }
 
 pp_status pp_create_device(const pp_config* cfg, int64_t n_terms, const uint64_t* x,
                            const uint64_t* z, const double* coef, pp_ctx** out) {
+  Range range_("pp_create_device");
   return create_common(cfg, n_terms, x, z, coef, true, out);
 }
 
 pp_status pp_import(pp_ctx* c, int64_t n_terms, const uint64_t* x, const uint64_t* z,
                     const double* coef) {
+  Range range_("pp_import");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (n_terms < 0) return fail(PP_ERR_ARG, "n_terms < 0");
   if (n_terms > 0 && (!x || !z || !coef)) return fail(PP_ERR_ARG, "null term arrays");
@@ -1448,6 +1464,7 @@ pp_status pp_destroy(pp_ctx* c) {
 
 pp_status pp_apply_layer(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
                          int symmetric_boundary) {
+  Range range_("pp_apply_layer");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (n_gates < 0 || (n_gates > 0 && (!gates || !theta)))
     return fail(PP_ERR_ARG, "bad gate arrays");
@@ -1552,6 +1569,7 @@ bool set_index_factor(pp_ctx* c, double f) {
 
 pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* theta,
                   double* chosen_scale) {
+  Range range_("pp_tune");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (n_gates < 0 || (n_gates > 0 && (!gates || !theta)))
     return fail(PP_ERR_ARG, "bad gate arrays");
@@ -1700,6 +1718,7 @@ pp_status pp_tune(pp_ctx* c, int n_gates, const pp_pauli* gates, const double* t
 }
 
 pp_status pp_canonicalize(pp_ctx* c) {
+  Range range_("pp_canonicalize");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (c->cfg.symmetry == PP_SYM_NONE) return fail(PP_ERR_STATE, "context has no symmetry");
   if (c->n_terms == 0) return PP_OK;
@@ -1713,11 +1732,13 @@ pp_status pp_canonicalize(pp_ctx* c) {
 }
 
 pp_status pp_merge(pp_ctx* c) {
+  Range range_("pp_merge");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   return merge_active(c, PP_SYM_NONE);
 }
 
 pp_status pp_truncate(pp_ctx* c, double eps, int max_weight) {
+  Range range_("pp_truncate");
   if (!c) return fail(PP_ERR_ARG, "ctx is null");
   if (!(eps >= 0.0)) return fail(PP_ERR_ARG, "eps must be >= 0");
   PP_TRY(ensure_merged(c));
@@ -1725,6 +1746,7 @@ pp_status pp_truncate(pp_ctx* c, double eps, int max_weight) {
 }
 
 pp_status pp_expect(pp_ctx* c, const double* bloch, double* out) {
+  Range range_("pp_expect");
   if (!c || !bloch || !out) return fail(PP_ERR_ARG, "null argument");
   const int n = c->n, W = c->W;
   for (int i = 0; i < 3 * n; ++i)
@@ -1803,6 +1825,7 @@ pp_status pp_num_terms(pp_ctx* c, int64_t* live, int64_t* stored) {
 
 pp_status pp_export(pp_ctx* c, int64_t capacity, uint64_t* x, uint64_t* z, double* coef,
                     int64_t* n_out) {
+  Range range_("pp_export");
   if (!c || !n_out) return fail(PP_ERR_ARG, "null argument");
   PP_TRY(ensure_merged(c));
   PP_TRY(read_ctl(c));

@@ -40,6 +40,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pp.h"
 #include "pp_internal.h"
 
@@ -202,6 +204,13 @@ Grow grow_reservation(pp_server* s, Job& j, size_t want) {
 // when the job released its memory to let others finish (it is queued
 // again).
 pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, bool* give_back) {
+  // one named range per job on the host timeline for profilers (NVTX)
+  char range_name[48];
+  snprintf(range_name, sizeof(range_name), "job %llu", (unsigned long long)j.id);
+  nvtxRangePushA(range_name);
+  struct PopRange {
+    ~PopRange() { nvtxRangePop(); }
+  } pop_range_;
   *give_back = false;
   pp_config cfg = j.cfg;
   cfg.cuda_stream = stream;
