@@ -403,11 +403,15 @@ typedef struct {
 } pp_job_result;
 
 /* A server with `slots` worker threads, each owning a CUDA stream on the
- * calling thread's current device.  Jobs are admitted oldest first among
- * those whose reservation fits in mem_budget_bytes minus the reservations of
- * running jobs; their kernels overlap on the device.  A running job waiting
- * for a larger reservation is served before any queued job is admitted, and
- * a queued job that younger ones have passed 8 times is not passed again.
+ * calling thread's current device.  Jobs are admitted among those whose
+ * reservation fits in mem_budget_bytes minus the reservations of running
+ * jobs, in order of predicted run time (a regression of the log run times of
+ * finished jobs on the job's layers, gates per layer, threshold, noise, n and
+ * group) less one natural-log unit per 10 s waited, so short jobs do not
+ * wait behind long ones and every job reaches the front; their kernels
+ * overlap on the device.  A running job waiting for a larger reservation is
+ * served before any queued job is admitted, and a queued job that jobs after
+ * it in that order have passed 8 times is not passed again.
  * default_job_bytes: reservation of jobs that name none; 0 = estimate each
  * from its observable (two tables with room for 4 n_terms strings plus fixed
  * buffers).  Errors: PP_ERR_ARG, PP_ERR_CUDA. */

@@ -2,10 +2,12 @@
 // product state) submitted from any host thread run concurrently on the GPU.
 //
 // Continuous batching: the server keeps `slots` worker threads, each with its
-// own CUDA stream.  A free worker takes the oldest queued job whose memory
-// reservation fits in what the running jobs leave of the budget, so a job that
-// arrives while others run starts as soon as a slot and memory are free, and
-// the kernels of different jobs overlap on the device.  A job runs in its own
+// own CUDA stream.  A free worker takes the queued job with the shortest
+// predicted run time (learned from the jobs finished so far, less a credit
+// for the time waited) whose memory reservation fits in what the running jobs
+// leave of the budget, so a job that arrives while others run starts as soon
+// as a slot and memory are free, and the kernels of different jobs overlap on
+// the device.  A job runs in its own
 // context (tables resident on the device for its whole life) whose memory
 // budget is its reservation; each of its layers runs as one persistent launch
 // on the share of the GPU's co-resident blocks it holds for that layer
@@ -62,12 +64,79 @@ struct Job {
   int restarts = 0;  // times the job gave its memory back and started over
   int bypassed = 0;  // younger jobs admitted while this one waited at the queue's head
   size_t want_next = 0;  // reservation asked for when the job gave its memory back
+  double feat[8] = {};   // features of the cost model (job_features)
   bool started = false;
   std::chrono::steady_clock::time_point t_submit, t_start;
 };
 
 struct Done {
   pp_job_result r{};
+};
+
+// Features of a job for the cost model: 1, log layers, log gates per layer,
+// log 1/eps (eps = 0 counts as 1e-12), per-gate or per-layer noise, noise x
+// log 1/eps, log n, and whether a group merges the strings.
+constexpr int kFeat = 8;
+void job_features(const pp_config& cfg, int n_layers, int n_gates, double* f) {
+  const double eps = cfg.coeff_eps > 1e-12 ? cfg.coeff_eps : 1e-12;
+  const double le = std::log(1.0 / eps);
+  const double noise = cfg.noise_mode != PP_NOISE_NONE ? 1.0 : 0.0;
+  f[0] = 1.0;
+  f[1] = std::log((double)std::max(n_layers, 1));
+  f[2] = std::log((double)std::max(n_gates, 1));
+  f[3] = le;
+  f[4] = noise;
+  f[5] = noise * le;
+  f[6] = std::log((double)std::max(cfg.n_qubits, 1));
+  f[7] = cfg.symmetry != PP_SYM_NONE ? 1.0 : 0.0;
+}
+
+// Predicted log run time of a job, learned from the jobs the server has
+// finished: ridge regression of log(run ms) on the features, pulled towards a
+// prior in which cost grows with layers x gates x eps^(-1/2).  Refitted after
+// every finished job (an 8 x 8 solve).
+struct CostModel {
+  double A[kFeat][kFeat] = {};  // sum of f f^T
+  double b[kFeat] = {};         // sum of f y
+  double beta[kFeat] = {-7.845, 0.887, 1.444, 0.703, 0.519, -0.438, -1.080, -0.338};
+  int n_obs = 0;
+
+  double predict(const double* f) const {
+    double v = 0.0;
+    for (int i = 0; i < kFeat; ++i) v += beta[i] * f[i];
+    return v;
+  }
+
+  void add(const double* f, double y) {
+    for (int i = 0; i < kFeat; ++i) {
+      b[i] += f[i] * y;
+      for (int k = 0; k < kFeat; ++k) A[i][k] += f[i] * f[k];
+    }
+    ++n_obs;
+    // (A + lambda I) beta = b + lambda beta0, by Gaussian elimination with
+    // partial pivoting; the prior keeps the system well posed
+    static const double prior[kFeat] = {-7.845, 0.887, 1.444, 0.703, 0.519, -0.438, -1.080, -0.338};
+    const double lambda = 1.0;
+    double M[kFeat][kFeat + 1];
+    for (int i = 0; i < kFeat; ++i) {
+      for (int k = 0; k < kFeat; ++k) M[i][k] = A[i][k] + (i == k ? lambda : 0.0);
+      M[i][kFeat] = b[i] + lambda * prior[i];
+    }
+    for (int c = 0; c < kFeat; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < kFeat; ++r)
+        if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+      if (std::fabs(M[piv][c]) < 1e-12) return;  // keep the previous fit
+      if (piv != c)
+        for (int k = 0; k <= kFeat; ++k) std::swap(M[c][k], M[piv][k]);
+      for (int r = 0; r < kFeat; ++r) {
+        if (r == c) continue;
+        const double m = M[r][c] / M[c][c];
+        for (int k = c; k <= kFeat; ++k) M[r][k] -= m * M[c][k];
+      }
+    }
+    for (int i = 0; i < kFeat; ++i) beta[i] = M[i][kFeat] / M[i][i];
+  }
 };
 
 using Clock = std::chrono::steady_clock;
@@ -91,6 +160,7 @@ struct pp_server {
   std::map<uint64_t, Done> results;
   int64_t running = 0, completed = 0;
   int units_free = 0;  // share units of the GPU's co-resident blocks not held by a layer
+  CostModel cost;      // predicted run times of queued jobs (admission order)
   std::mutex mu;
   std::condition_variable cv_work;  // workers: a job or memory became available
   std::condition_variable cv_done;  // waiters: a job finished
@@ -123,18 +193,39 @@ size_t estimate_job_bytes(const pp_config& cfg, int64_t terms) {
   return round_mib(2.0 * table + (double)terms * (16.0 * W + row) + (double)kMiB);
 }
 
-// Oldest queued job whose reservation fits; nullptr if none.  Jobs waiting
-// to grow come first, and a job passed kMaxBypass times blocks younger ones.
+// Admission order: the lowest predicted cost first, less one (natural-log)
+// unit for every kAgeSeconds a job has waited, so that cheap jobs do not
+// queue behind expensive ones and an expensive job still comes to the front.
+// A job that gave its memory back keeps its place (it has waited longest).
+constexpr double kAgeSeconds = 10.0;
+
+double admission_key(const pp_server* s, const Job& j, Clock::time_point now) {
+  const double waited = std::chrono::duration<double>(now - j.t_submit).count();
+  const double given_back = j.restarts > 0 ? -1e9 : 0.0;  // back at the head
+  return s->cost.predict(j.feat) - waited / kAgeSeconds + given_back;
+}
+
+// The queued job first in admission order whose reservation fits; nullptr if
+// none.  Jobs waiting to grow come first, and a job passed kMaxBypass times by
+// jobs after it in that order blocks them.
 std::unique_ptr<Job> take_fitting(pp_server* s) {
   if (s->growing > 0) return nullptr;
-  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-    if (s->reserved + (*it)->reserve <= s->budget) {
-      for (auto older = s->queue.begin(); older != it; ++older) (*older)->bypassed++;
-      std::unique_ptr<Job> j = std::move(*it);
+  const Clock::time_point now = Clock::now();
+  std::vector<std::pair<double, size_t>> order;
+  order.reserve(s->queue.size());
+  for (size_t k = 0; k < s->queue.size(); ++k)
+    order.emplace_back(admission_key(s, *s->queue[k], now), k);
+  std::sort(order.begin(), order.end());
+  for (size_t r = 0; r < order.size(); ++r) {
+    Job& j = *s->queue[order[r].second];
+    if (s->reserved + j.reserve <= s->budget) {
+      for (size_t q = 0; q < r; ++q) s->queue[order[q].second]->bypassed++;
+      auto it = s->queue.begin() + (std::ptrdiff_t)order[r].second;
+      std::unique_ptr<Job> out = std::move(*it);
       s->queue.erase(it);
-      return j;
+      return out;
     }
-    if ((*it)->bypassed >= kMaxBypass) return nullptr;
+    if (j.bypassed >= kMaxBypass) return nullptr;
   }
   return nullptr;
 }
@@ -325,6 +416,7 @@ void worker_main(pp_server* s) {
       r.reserved_bytes = j->reserve;
       r.grows = j->grows;
       r.restarts = j->restarts;
+      if (st == PP_OK && r.run_ms > 0.0) s->cost.add(j->feat, std::log(r.run_ms));
       s->results[j->id].r = r;
       s->completed++;
       s->cv_done.notify_all();
@@ -383,6 +475,7 @@ pp_status pp_submit(pp_server* s, const pp_job* job, uint64_t* job_id) {
   j->bloch.assign(job->bloch, job->bloch + 3 * cfg.n_qubits);
   j->n_layers = job->n_layers;
   j->boundary = job->symmetric_boundary;
+  job_features(cfg, job->n_layers, job->n_layer_gates, j->feat);
   j->reserve = job->mem_bytes ? job->mem_bytes
                               : (s->default_reserve ? s->default_reserve
                                                     : estimate_job_bytes(cfg, job->n_terms));
