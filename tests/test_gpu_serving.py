@@ -196,3 +196,26 @@ def test_growing_job_is_not_starved_by_a_stream_of_small_jobs():
     for r, wl in zip(rs, small):
         assert r["status"] == 0, r["message"]
         assert r["value"] == pytest.approx(alone(wl), abs=1e-10)
+
+
+def test_short_job_is_admitted_before_a_long_one_submitted_earlier():
+    """Admission follows the predicted run time: on a one-slot server busy
+    with a first job, an expensive job (12 steps at n = 32, eps 1e-5) and then
+    a cheap one (3 steps at n = 12, eps 1e-3) are queued; the cheap one starts
+    first although it arrived later, and both results equal the jobs alone."""
+    first = workload("ring", 16, 8, 1e-4, 7)
+    slow = workload("ring", 32, 12, 1e-5, 8)
+    fast = workload("ring", 12, 3, 1e-3, 9)
+    server = pp.pp_server_create(1, 8 << 30, 0)
+    keep, ids = [], []
+    for wl in (first, slow, fast):
+        job, bufs = job_of(wl)
+        keep.append(bufs)
+        ids.append(pp.pp_submit(server, job))
+    res = [pp.pp_server_wait(server, j) for j in ids]
+    pp.pp_server_destroy(server)
+    for r in res:
+        assert r["status"] == 0, r["message"]
+    assert res[2]["queue_ms"] < res[1]["queue_ms"]
+    for r, wl in zip(res, (first, slow, fast)):
+        assert r["value"] == pytest.approx(alone(wl), abs=1e-10)
