@@ -31,7 +31,14 @@ NOISE_NONE, NOISE_PER_GATE, NOISE_PER_LAYER = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.cpp into liboracle.so (plain g++, no FMA contraction)."""
+    """Compile oracle.cpp into liboracle.so (plain g++, no FMA contraction).
+
+    With PP_ORACLE_SO set, that prebuilt library is used instead and nothing is
+    compiled: the mutation test points the pins at copies of the oracle with a
+    planted mistake this way."""
+    override = os.environ.get("PP_ORACLE_SO")
+    if override:
+        return override
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
                _SRC, "-o", _LIB + ".tmp"]
@@ -44,8 +51,7 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_LIB)
+    lib = ctypes.CDLL(build())
     P = ctypes.c_void_p
     u64p = ctypes.POINTER(ctypes.c_uint64)
     f64p = ctypes.POINTER(ctypes.c_double)

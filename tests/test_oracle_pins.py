@@ -522,6 +522,102 @@ def test_batched_truncation_keeps_a_term_if_any_column_is_large(oracle_lib):
     assert got == {"ZII": (1e-4, 2e-2), "IYI": (0.5, 0.5)}
 
 
+# -------------------------- ingest, the update count, batched merging
+
+def test_ingest_accumulates_repeated_strings(oracle_lib):
+    """Algorithm 1 step 1 starts from O = sum_s c_s s: a string listed twice
+    stands for the sum of its coefficients.  The ingested table holds the
+    sums (single column and batched rows), and <O> after a random circuit on
+    a mixed product state is the density-matrix value of the same list of
+    terms."""
+    n = 4
+    terms = [("ZIII", 0.25), ("XYII", 0.5), ("ZIII", 0.5), ("IIXZ", 1.0), ("XYII", -0.125)]
+    x, z = pi.to_masks([t for t, _ in terms], n)
+    st = oracle_lib.OracleState(n, x, z, np.array([c for _, c in terms]))
+    ex, ez, ec = st.export()
+    assert dict(zip(pi.from_masks(ex, ez, n), ec.tolist())) == {
+        "ZIII": 0.75, "XYII": 0.375, "IIXZ": 1.0}
+    circ = pi.random_circuit(n, n_layers=2, gates_per_layer=5, seed=41, max_support=2)
+    state = pi.random_product_state(n, 42)
+    for li in reversed(range(len(circ.layers))):
+        gx, gz, th = circ.gate_arrays(li)
+        st.apply_layer(gx, gz, th)
+    ref = sv.density_expectations(n, circ.layers, terms, state.bloch)[-1]
+    assert st.expect(state.bloch) == pytest.approx(ref, abs=1e-12)
+
+    coef = np.array([[0.25, -1.0], [0.5, 0.0], [0.5, 2.0], [1.0, 1.0], [-0.125, 0.5]])
+    bst = oracle_lib.BatchedOracleState(n, 2, x, z, coef)
+    bx, bz, bc = bst.export()
+    assert dict(zip(pi.from_masks(bx, bz, n), map(tuple, bc.tolist()))) == {
+        "ZIII": (0.75, 1.0), "XYII": (0.375, 0.5), "IIXZ": (1.0, 1.0)}
+
+
+def test_update_count_is_the_live_terms_entering_each_gate(oracle_lib):
+    """The throughput unit: one update is one live term entering one gate.
+    Closed form for X_0 under RZ_0, RZ_0, RZ_1 (Heisenberg order): one term
+    enters the first gate and leaves it as {X_0, Y_0}, two enter each later
+    gate (1, 3, 5).  With a threshold that drops the sin branch, one term
+    enters every gate (1, 2, 3).  On a truncated ring circuit the count grows
+    at every gate by the number of terms stored just before it."""
+    n = 2
+    x, z = pi.to_masks(["XI"], n)
+    gates = [pi.pauli(n, {0: "Z"}), pi.pauli(n, {0: "Z"}), pi.pauli(n, {1: "Z"})]
+    for eps, th, want in [(0.0, 0.7, [1, 3, 5]), (0.5, 0.1, [1, 2, 3])]:
+        st = oracle_lib.OracleState(n, x, z, np.array([1.0]), eps=eps)
+        bst = oracle_lib.BatchedOracleState(n, 2, x, z, np.array([[1.0, 0.5]]), eps=eps)
+        got, bgot = [], []
+        for g in gates:
+            gx, gz = pi.to_masks([g], n)
+            st.apply_gate(gx[0], gz[0], th)
+            bst.apply_layer(gx, gz, np.array([[th, th]]))
+            got.append(st.updates)
+            bgot.append(bst.updates)
+        assert got == want and bgot == want
+
+    wl = pi.config1_ring(n=8, steps=2, eps=1e-3, max_weight=4)
+    x, z, c = wl.observable.arrays()
+    st = oracle_lib.OracleState(8, x, z, c, eps=wl.eps, max_weight=wl.max_weight)
+    bst = oracle_lib.BatchedOracleState(8, 1, x, z, c[:, None], eps=wl.eps,
+                                        max_weight=wl.max_weight)
+    for layer in reversed(range(2)):
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        for g in reversed(range(len(th))):
+            before, bbefore = len(st), len(bst)
+            u, bu = st.updates, bst.updates
+            st.apply_gate(gx[g], gz[g], th[g])
+            bst.apply_layer(gx[g:g + 1], gz[g:g + 1], th[g:g + 1, None])
+            assert st.updates - u == before and bst.updates - bu == bbefore
+    assert st.updates > 100
+
+
+def test_batched_symmetry_merge_keeps_every_column_exact(oracle_lib):
+    """Batched rows merged by Z_n representatives after every ring step (Eq.
+    O-merging, column by column): without truncation every column's <O> is
+    the state-vector value for its own angles (Theorem 1; the Neel state is
+    not invariant, so the overlap is the orbit average), and the merged
+    table is smaller than the unmerged one."""
+    n, B, L = 6, 3, 2
+    angles = _ring_angles(B, 5)
+    gx, gz, _ = pi.Circuit(n, [pi.ring_layer(n, 0, 0, 0)]).gate_arrays(0)
+    obs = pi.mean_z(n)
+    x, z, c = obs.arrays()
+    state = pi.neel_state(n)
+    th = _ring_theta(n, angles)
+    rows = np.repeat(c[:, None], B, axis=1)
+    merged = oracle_lib.BatchedOracleState(n, B, x, z, rows, group=1)
+    plain = oracle_lib.BatchedOracleState(n, B, x, z, rows)
+    for _ in range(L):
+        merged.apply_layer(gx, gz, th, group=1)
+        plain.apply_layer(gx, gz, th)
+    got = merged.expect(state.bloch, 1)
+    for b in range(B):
+        layer = [(s, float(th[g, b])) for g, (s, _) in enumerate(pi.ring_layer(n, 0, 0, 0))]
+        ref = sv.statevector_expectations([layer] * L, obs.terms, state.bloch)[-1]
+        assert got[b] == pytest.approx(ref, abs=1e-12)
+    assert len(set(np.round(got, 9))) == B
+    assert len(merged) < len(plain)
+
+
 # ------------------------------------------ the stored expected values
 
 def _trajectory(oracle_lib, wl, group, layers):
