@@ -14,8 +14,11 @@ already in device memory; ``e2e`` goes through the host-buffer C-ABI calls
 run the job without instrumentation.  ``roofline`` is for the layer kernel,
 timed with CUDA events around every layer kernel on the context's stream in a
 separate pass of the same jobs.  ``cpu_baseline`` times the CPU
-oracle on a bounded prefix of the same workload.  With N > 1 (torchrun) every
-rank runs an independent replica of the job (the path does not shard).
+oracle on a bounded prefix of the same workload.  ``served`` (one GPU only)
+is the serving part of the metric: a scaled Poisson stream of 300 jobs
+through pp_submit after the main job, with jobs/s and latency p50/p99
+(``--no-serving`` leaves it out).  With N > 1 (torchrun) every rank runs an
+independent replica of the job (the path does not shard).
 """
 import argparse
 import json
@@ -386,6 +389,12 @@ def bench_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    served = None
+    if world == 1 and not args.no_serving:
+        try:
+            served = served_summary(pp)
+        except Exception as e:  # the headline line is printed whatever happens here
+            served = {"error": f"{type(e).__name__}: {e}"}
     cpu = cpu_baseline(seconds=args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -427,6 +436,7 @@ def bench_ours(args):
                                "same jobs after the timed regions"},
         "clocks": clk,
         "cpu_baseline": cpu,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -570,15 +580,14 @@ def serving_specs_full(n_jobs, rate, seed=0):
     return out
 
 
-def bench_serving(args):
-    import torch
-    import paper_2512_12094_gb300 as pp
-    torch.cuda.set_device(0)
-    pp.build()
-    pp.load()
-    full = args.serving_full > 0
-    specs = serving_specs_full(args.serving_full, args.rate) if full else \
-        serving_specs(args.serving, args.rate)
+def serve_stream(pp, specs, slots, full, check_every=None):
+    """Serve `specs` (arrival time, workload) through pp_submit on a server
+    with `slots` workers and a 150 GB budget, submitting each job at its
+    arrival time; then run a sample of the same jobs (every check_every-th;
+    by default all of them for the scaled stream and about 50 for the
+    full-size one) one after the other on one slot to check their results
+    against the job run alone.  Returns (results, wall s, results alone,
+    wall s alone, the sample's indices or None for all)."""
     jobs = []
     for _, wl in specs:
         cfg = pp.pp_config_default(n_qubits=wl.circuit.n, symmetry=wl.symmetry, coeff_eps=wl.eps,
@@ -618,19 +627,57 @@ def bench_serving(args):
                   file=sys.stderr, flush=True)
 
     if not full:
-        warm, _ = run(args.slots, False)  # warm-up (builds graphs, pools)
+        warm, _ = run(slots, False)  # warm-up (builds graphs, pools)
         report_failures("warm-up", warm)
-    res, wall = run(args.slots, True)
+    res, wall = run(slots, True)
     report_failures("timed", res)
-    lat = np.array([r["latency_ms"] for r in res])
-    # the same jobs one after the other on one slot (every job for the scaled
-    # stream; for the full-size stream a sample of about 50, whose sequential
-    # time is not reported)
-    subset = None if not full else list(range(0, len(jobs), max(1, len(jobs) // 50)))
+    if check_every is None and full:
+        check_every = max(1, len(jobs) // 50)
+    subset = None if check_every is None else list(range(0, len(jobs), check_every))
     seq, seq_wall = run(1, False, subset)
+    return res, wall, seq, seq_wall, subset
+
+
+def served_max_diff(res, seq, subset):
     pairs = zip(res if subset is None else [res[k] for k in subset], seq)
     ok = [(a, b) for a, b in pairs if a["status"] == 0 and b["status"] == 0]
-    err = max((abs(a["value"] - b["value"]) for a, b in ok), default=None)
+    return max((abs(a["value"] - b["value"]) for a, b in ok), default=None)
+
+
+def served_summary(pp, n_jobs=300, rate=200.0, slots=8):
+    """The serving part of the metric, measured beside the headline job: the
+    scaled Poisson stream (n_jobs jobs at `rate`/s, every job well under a
+    second) through pp_submit.  Jobs/s over the stream's wall time, latency
+    p50/p99 from submission to result, and every result against the same
+    job run alone."""
+    specs = serving_specs(n_jobs, rate)
+    res, wall, seq, _, subset = serve_stream(pp, specs, slots, False, check_every=5)
+    lat = np.array([r["latency_ms"] for r in res])
+    return {"workload": "serving_stream_scaled", "jobs": len(res), "rate_per_s": rate,
+            "slots": slots,
+            "sizes": "ring n in {16,32,64,128}, <= 20 steps, weight <= 8, eps >= 1e-4; "
+                     "all-to-all Heisenberg n in {8,10,12,16}, <= 4 steps",
+            "jobs_per_s": len(res) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "failed": int(sum(r["status"] != 0 for r in res)),
+            "max_abs_diff_vs_alone": served_max_diff(res, seq, subset),
+            "checked_alone": len(seq),
+            "timing": "host wall clock from each job's submission to its result"}
+
+
+def bench_serving(args):
+    import torch
+    import paper_2512_12094_gb300 as pp
+    torch.cuda.set_device(0)
+    pp.build()
+    pp.load()
+    full = args.serving_full > 0
+    specs = serving_specs_full(args.serving_full, args.rate) if full else \
+        serving_specs(args.serving, args.rate)
+    res, wall, seq, seq_wall, subset = serve_stream(pp, specs, args.slots, full)
+    lat = np.array([r["latency_ms"] for r in res])
+    err = served_max_diff(res, seq, subset)
     line = {"metric": "served_jobs_per_s", "value": len(res) / wall, "unit": "jobs/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "serving_stream_full_sizes" if full else "serving_stream_scaled",
@@ -991,6 +1038,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave out the scaled serving stream measured after the main job")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
     ap.add_argument("--trace-layers", action="store_true",
                     help="one JSON line per layer of the config-1 job (no timing contract)")
