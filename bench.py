@@ -17,7 +17,9 @@ separate pass of the same jobs.  ``cpu_baseline`` times the CPU
 oracle on a bounded prefix of the same workload.  ``served`` (one GPU only)
 is the serving part of the metric: a scaled Poisson stream of 300 jobs
 through pp_submit after the main job, with jobs/s and latency p50/p99
-(``--no-serving`` leaves it out).  With N > 1 (torchrun) every rank runs an
+(``--no-serving`` leaves it out).  ``other_workloads`` (one GPU only) times the
+all-to-all n=64, the batched-angle ring n=64 and the XXZ n=36 workloads once
+each (``--no-others`` leaves them out).  With N > 1 (torchrun) every rank runs an
 independent replica of the job (the path does not shard).
 """
 import argparse
@@ -395,6 +397,12 @@ def bench_ours(args):
             served = served_summary(pp)
         except Exception as e:  # the headline line is printed whatever happens here
             served = {"error": f"{type(e).__name__}: {e}"}
+    others = None
+    if world == 1 and not args.no_others:
+        try:
+            others = other_workloads_summary(pp)
+        except Exception as e:  # the headline line is printed whatever happens here
+            others = {"error": f"{type(e).__name__}: {e}"}
     cpu = cpu_baseline(seconds=args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -437,6 +445,7 @@ def bench_ours(args):
         "clocks": clk,
         "cpu_baseline": cpu,
         "served": served,
+        "other_workloads": others,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -756,6 +765,69 @@ def _timed_run(pp, make, layers, boundary=True, bloch=None):
     return t0.elapsed_time(t1), st, live, val
 
 
+def _packed_layers(pp, wl, count=None):
+    """The workload's layers in application (Heisenberg) order as (packed
+    gates, angles), the first `count` of them if given."""
+    L = len(wl.circuit.layers)
+    out = []
+    for k, layer in enumerate(reversed(range(L))):
+        if count is not None and k >= count:
+            break
+        gx, gz, th = wl.circuit.gate_arrays(layer)
+        out.append((pp.pack_gates(gx, gz), th))
+    return out
+
+
+def _ring64_batched(pp):
+    """Ring n=64 with 256 angle sets in [0, pi/2] (seed 0): (packed gates,
+    angles [192, 256], x, z, single-column coefficients, rows [n, 256])."""
+    n, B = 64, 256
+    angles = pi.batched_ring_angles(B, 0)
+    gx, gz, _ = pi.Circuit(n, [pi.ring_layer(n, 0.0, 0.0, 0.0)]).gate_arrays(0)
+    th = np.zeros((3 * n, B))
+    th[:n], th[n:2 * n], th[2 * n:] = angles[:, 0], angles[:, 1], angles[:, 2]
+    x, z, c = pi.mean_z(n).arrays()
+    return pp.pack_gates(gx, gz), th, x, z, c, np.repeat(c[:, None], B, axis=1)
+
+
+def other_workloads_summary(pp):
+    """The other full-size workloads through the same C ABI, measured beside
+    the headline job: one warm-up run, then one run timed with CUDA events
+    (context creation included).
+    * all-to-all Heisenberg n=64, 10 steps (60,480 gates), per-gate damping
+      p=0.01, eps 1e-5, Neel, merged under S_64;
+    * ring n=64 with 256 angle sets (eps 1e-5 on any column), its first three
+      steps, FP64 and FP32 rows (the table grows about tenfold per step and
+      the 30 steps do not fit one GPU);
+    * all-to-all XXZ n=36, eps 0.05, merged under S_36 after each of its
+      first 16 XX/YY/ZZ sublayers."""
+    out = {}
+    wl = pi.config2_all_to_all()
+    layers = _packed_layers(pp, wl)
+    make = lambda: pp.Propagator.from_workload(wl, symmetry=2)  # noqa: E731
+    _timed_run(pp, make, layers[:1])
+    ms, st, live, val = _timed_run(pp, make, layers, bloch=wl.state.bloch)
+    out["a2a64_S64_per_gate_noise_10steps"] = {
+        "ms": ms, "value": st["gate_updates"] / (ms / 1e3), "unit": "updates/s",
+        "gates": len(layers) * 6048, "expect": val, "live_terms": live}
+    packed, th, x, z, _, rows = _ring64_batched(pp)
+    for f32 in (False, True):
+        make = lambda: pp.Propagator(64, x, z, rows, eps=1e-5, batch=256, f32=f32)  # noqa: E731
+        _timed_run(pp, make, [(packed, th)])
+        ms, st, live, _ = _timed_run(pp, make, [(packed, th)] * 3)
+        out["ring64_B256_%s_3steps" % ("fp32" if f32 else "fp64")] = {
+            "ms": ms, "value": st["gate_updates"] * 256 / (ms / 1e3),
+            "unit": "column updates/s (live strings x gates x 256 columns)", "live_terms": live}
+    wl = pi.xxz_all_to_all(36, 0.05, 6, eps=0.05, symmetry=2, split=True)
+    layers = _packed_layers(pp, wl, 16)
+    make = lambda: pp.Propagator.from_workload(wl, symmetry=2)  # noqa: E731
+    _timed_run(pp, make, layers[:3])
+    ms, st, live, val = _timed_run(pp, make, layers, bloch=wl.state.bloch)
+    out["xxz36_S36_16_sublayers"] = {"ms": ms, "value": st["gate_updates"] / (ms / 1e3),
+                                     "unit": "updates/s", "S2_over_S02": val, "live_terms": live}
+    return out
+
+
 def bench_workload(args):
     """The other workloads through the same C ABI, one JSON line each (one
     GPU; not the headline).  a2a64: all-to-all Heisenberg n=64, 10 steps,
@@ -774,14 +846,7 @@ def bench_workload(args):
     pp.load()
 
     def packed_layers(wl, count=None):
-        L = len(wl.circuit.layers)
-        out = []
-        for k, layer in enumerate(reversed(range(L))):
-            if count is not None and k >= count:
-                break
-            gx, gz, th = wl.circuit.gate_arrays(layer)
-            out.append((pp.pack_gates(gx, gz), th))
-        return out
+        return _packed_layers(pp, wl, count)
 
     def line(name, ms, updates, extra):
         d = {"metric": "pauli_term_gate_updates_per_s", "value": updates / (ms / 1e3),
@@ -804,14 +869,7 @@ def bench_workload(args):
                                                  "gates_per_run": len(layers) * 6048})
     if "batched64" in names or "columns64" in names:
         n, B, steps = 64, 256, 3
-        angles = pi.batched_ring_angles(B, 0)
-        layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
-        gx, gz, _ = pi.Circuit(n, [layer]).gate_arrays(0)
-        th = np.zeros((3 * n, B))
-        th[:n], th[n:2 * n], th[2 * n:] = angles[:, 0], angles[:, 1], angles[:, 2]
-        x, z, c = pi.mean_z(n).arrays()
-        coef = np.repeat(c[:, None], B, axis=1)
-        packed = pp.pack_gates(gx, gz)
+        packed, th, x, z, c, coef = _ring64_batched(pp)
         for f32 in ((False, True) if "batched64" in names else ()):
             make = lambda: pp.Propagator(n, x, z, coef, eps=1e-5, batch=B, f32=f32)  # noqa: E731
             _timed_run(pp, make, [(packed, th)])
@@ -918,14 +976,7 @@ def bench_workload(args):
     if "rows64" in names:
         # batched rows (ring n=64, B = 256, 3 steps) merged by hash and by sort
         n, B, steps = 64, 256, 3
-        angles = pi.batched_ring_angles(B, 0)
-        layer = pi.ring_layer(n, 0.0, 0.0, 0.0)
-        gx, gz, _ = pi.Circuit(n, [layer]).gate_arrays(0)
-        th = np.zeros((3 * n, B))
-        th[:n], th[n:2 * n], th[2 * n:] = angles[:, 0], angles[:, 1], angles[:, 2]
-        x, z, c = pi.mean_z(n).arrays()
-        coef = np.repeat(c[:, None], B, axis=1)
-        packed = pp.pack_gates(gx, gz)
+        packed, th, x, z, c, coef = _ring64_batched(pp)
         for f32 in (False, True):
             for method, label in ((pp.MERGE_HASH, "hash"), (pp.MERGE_SORT, "sort")):
                 make = lambda: pp.Propagator(n, x, z, coef, symmetry=1, eps=1e-5, batch=B,  # noqa: E731
@@ -1040,6 +1091,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave out the scaled serving stream measured after the main job")
+    ap.add_argument("--no-others", action="store_true",
+                    help="leave out the other workloads measured after the main job")
     ap.add_argument("--only", default="both", choices=sorted(GROUPS))
     ap.add_argument("--trace-layers", action="store_true",
                     help="one JSON line per layer of the config-1 job (no timing contract)")
