@@ -45,6 +45,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pp.h"
+#include "pp_admission.h"
 #include "pp_internal.h"
 
 namespace {
@@ -64,79 +65,13 @@ struct Job {
   int restarts = 0;  // times the job gave its memory back and started over
   int bypassed = 0;  // younger jobs admitted while this one waited at the queue's head
   size_t want_next = 0;  // reservation asked for when the job gave its memory back
-  double feat[8] = {};   // features of the cost model (job_features)
+  double feat[ppadm::kFeat] = {};  // features of the cost model (job_features)
   bool started = false;
   std::chrono::steady_clock::time_point t_submit, t_start;
 };
 
 struct Done {
   pp_job_result r{};
-};
-
-// Features of a job for the cost model: 1, log layers, log gates per layer,
-// log 1/eps (eps = 0 counts as 1e-12), per-gate or per-layer noise, noise x
-// log 1/eps, log n, and whether a group merges the strings.
-constexpr int kFeat = 8;
-void job_features(const pp_config& cfg, int n_layers, int n_gates, double* f) {
-  const double eps = cfg.coeff_eps > 1e-12 ? cfg.coeff_eps : 1e-12;
-  const double le = std::log(1.0 / eps);
-  const double noise = cfg.noise_mode != PP_NOISE_NONE ? 1.0 : 0.0;
-  f[0] = 1.0;
-  f[1] = std::log((double)std::max(n_layers, 1));
-  f[2] = std::log((double)std::max(n_gates, 1));
-  f[3] = le;
-  f[4] = noise;
-  f[5] = noise * le;
-  f[6] = std::log((double)std::max(cfg.n_qubits, 1));
-  f[7] = cfg.symmetry != PP_SYM_NONE ? 1.0 : 0.0;
-}
-
-// Predicted log run time of a job, learned from the jobs the server has
-// finished: ridge regression of log(run ms) on the features, pulled towards a
-// prior in which cost grows with layers x gates x eps^(-1/2).  Refitted after
-// every finished job (an 8 x 8 solve).
-struct CostModel {
-  double A[kFeat][kFeat] = {};  // sum of f f^T
-  double b[kFeat] = {};         // sum of f y
-  double beta[kFeat] = {-7.845, 0.887, 1.444, 0.703, 0.519, -0.438, -1.080, -0.338};
-  int n_obs = 0;
-
-  double predict(const double* f) const {
-    double v = 0.0;
-    for (int i = 0; i < kFeat; ++i) v += beta[i] * f[i];
-    return v;
-  }
-
-  void add(const double* f, double y) {
-    for (int i = 0; i < kFeat; ++i) {
-      b[i] += f[i] * y;
-      for (int k = 0; k < kFeat; ++k) A[i][k] += f[i] * f[k];
-    }
-    ++n_obs;
-    // (A + lambda I) beta = b + lambda beta0, by Gaussian elimination with
-    // partial pivoting; the prior keeps the system well posed
-    static const double prior[kFeat] = {-7.845, 0.887, 1.444, 0.703, 0.519, -0.438, -1.080, -0.338};
-    const double lambda = 1.0;
-    double M[kFeat][kFeat + 1];
-    for (int i = 0; i < kFeat; ++i) {
-      for (int k = 0; k < kFeat; ++k) M[i][k] = A[i][k] + (i == k ? lambda : 0.0);
-      M[i][kFeat] = b[i] + lambda * prior[i];
-    }
-    for (int c = 0; c < kFeat; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < kFeat; ++r)
-        if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
-      if (std::fabs(M[piv][c]) < 1e-12) return;  // keep the previous fit
-      if (piv != c)
-        for (int k = 0; k <= kFeat; ++k) std::swap(M[c][k], M[piv][k]);
-      for (int r = 0; r < kFeat; ++r) {
-        if (r == c) continue;
-        const double m = M[r][c] / M[c][c];
-        for (int k = c; k <= kFeat; ++k) M[r][k] -= m * M[c][k];
-      }
-    }
-    for (int i = 0; i < kFeat; ++i) beta[i] = M[i][kFeat] / M[i][i];
-  }
 };
 
 using Clock = std::chrono::steady_clock;
@@ -160,7 +95,7 @@ struct pp_server {
   std::map<uint64_t, Done> results;
   int64_t running = 0, completed = 0;
   int units_free = 0;  // share units of the GPU's co-resident blocks not held by a layer
-  CostModel cost;      // predicted run times of queued jobs (admission order)
+  ppadm::CostModel cost;  // predicted run times of queued jobs (admission order)
   std::mutex mu;
   std::condition_variable cv_work;  // workers: a job or memory became available
   std::condition_variable cv_done;  // waiters: a job finished
@@ -169,14 +104,7 @@ struct pp_server {
 
 namespace {
 
-constexpr int kMaxBypass = 8;
 constexpr size_t kMiB = (size_t)1 << 20;
-// The GPU's co-resident blocks, in share units handed to the layers of
-// running jobs: a job's persistent layer launch holds its units while it
-// runs, and the units held at any time add up to at most the whole GPU, so
-// the cooperative launches of all jobs fit at once.
-constexpr int kShareUnits = 1024;
-
 size_t round_mib(double b) { return ((size_t)std::ceil(b / (double)kMiB) + 1) * kMiB; }
 
 // Device memory of a context holding `terms` strings: two tables with room
@@ -193,41 +121,36 @@ size_t estimate_job_bytes(const pp_config& cfg, int64_t terms) {
   return round_mib(2.0 * table + (double)terms * (16.0 * W + row) + (double)kMiB);
 }
 
-// Admission order: the lowest predicted cost first, less one (natural-log)
-// unit for every kAgeSeconds a job has waited, so that cheap jobs do not
-// queue behind expensive ones and an expensive job still comes to the front.
-// A job that gave its memory back keeps its place (it has waited longest).
-constexpr double kAgeSeconds = 10.0;
-
-double admission_key(const pp_server* s, const Job& j, Clock::time_point now) {
-  const double waited = std::chrono::duration<double>(now - j.t_submit).count();
-  const double given_back = j.restarts > 0 ? -1e9 : 0.0;  // back at the head
-  return s->cost.predict(j.feat) - waited / kAgeSeconds + given_back;
-}
-
+// Admission order (ppadm::admission_key): the lowest predicted cost first,
+// less one (natural-log) unit for every kAgeSeconds a job has waited, so that
+// cheap jobs do not queue behind expensive ones and an expensive job still
+// comes to the front.  A job that gave its memory back keeps its place (it
+// has waited longest).
+//
 // The queued job first in admission order whose reservation fits; nullptr if
 // none.  Jobs waiting to grow come first, and a job passed kMaxBypass times by
-// jobs after it in that order blocks them.
+// jobs after it in that order blocks them (ppadm::pick_admission).
 std::unique_ptr<Job> take_fitting(pp_server* s) {
   if (s->growing > 0) return nullptr;
   const Clock::time_point now = Clock::now();
-  std::vector<std::pair<double, size_t>> order;
-  order.reserve(s->queue.size());
-  for (size_t k = 0; k < s->queue.size(); ++k)
-    order.emplace_back(admission_key(s, *s->queue[k], now), k);
-  std::sort(order.begin(), order.end());
-  for (size_t r = 0; r < order.size(); ++r) {
-    Job& j = *s->queue[order[r].second];
-    if (s->reserved + j.reserve <= s->budget) {
-      for (size_t q = 0; q < r; ++q) s->queue[order[q].second]->bypassed++;
-      auto it = s->queue.begin() + (std::ptrdiff_t)order[r].second;
-      std::unique_ptr<Job> out = std::move(*it);
-      s->queue.erase(it);
-      return out;
-    }
-    if (j.bypassed >= kMaxBypass) return nullptr;
+  const size_t q = s->queue.size();
+  std::vector<double> key(q);
+  std::vector<char> fits(q);
+  std::vector<int> bypassed(q);
+  for (size_t k = 0; k < q; ++k) {
+    const Job& j = *s->queue[k];
+    const double waited = std::chrono::duration<double>(now - j.t_submit).count();
+    key[k] = ppadm::admission_key(s->cost.predict(j.feat), waited, j.restarts > 0);
+    fits[k] = s->reserved + j.reserve <= s->budget;
+    bypassed[k] = j.bypassed;
   }
-  return nullptr;
+  const long pick = ppadm::pick_admission(key, fits, bypassed);
+  for (size_t k = 0; k < q; ++k) s->queue[k]->bypassed = bypassed[k];
+  if (pick < 0) return nullptr;
+  auto it = s->queue.begin() + (std::ptrdiff_t)pick;
+  std::unique_ptr<Job> out = std::move(*it);
+  s->queue.erase(it);
+  return out;
 }
 
 // Share units for one layer of a job whose launch would use the fraction
@@ -242,14 +165,9 @@ std::unique_ptr<Job> take_fitting(pp_server* s) {
 // ends.
 int acquire_units(pp_server* s, double wanted) {
   std::unique_lock<std::mutex> lock(s->mu);
-  const int floor_units = std::max(1, kShareUnits / s->slots);
   for (;;) {
-    const int fair =
-        std::max(floor_units, kShareUnits / (int)std::max<int64_t>(1, s->running));
-    const int want =
-        std::max(floor_units, std::min(fair, (int)std::ceil(wanted * kShareUnits)));
-    if (s->units_free >= floor_units) {
-      const int take = std::min(want, s->units_free);
+    const int take = ppadm::share_units(s->slots, s->running, wanted, s->units_free);
+    if (take > 0) {
       s->units_free -= take;
       return take;
     }
@@ -352,7 +270,7 @@ pp_status run_job(pp_server* s, Job& j, cudaStream_t stream, pp_job_result& r, b
       // another job needs in order to finish.
       const double wanted = ppk::layer_fraction_wanted(ctx);
       const int units = wanted > 0.0 ? acquire_units(s, wanted) : 0;
-      if (units > 0) ppk::set_grid_fraction(ctx, (double)units / kShareUnits);
+      if (units > 0) ppk::set_grid_fraction(ctx, (double)units / ppadm::kShareUnits);
       st = pp_apply_layer(ctx, (int)j.gates.size(), j.gates.data(), j.theta.data(), j.boundary);
       if (units > 0) release_units(s, units);
       if (st != PP_ERR_CAPACITY || !grow_or_stop(st)) break;
@@ -440,7 +358,7 @@ pp_status pp_server_create(int slots, size_t mem_budget_bytes, size_t default_jo
   s->budget = mem_budget_bytes;
   s->slots = slots;
   s->default_reserve = default_job_bytes;  // 0: each job's reservation is estimated
-  s->units_free = kShareUnits;
+  s->units_free = ppadm::kShareUnits;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     ppk::set_last_error("pp_server_create: no CUDA device");
@@ -475,7 +393,7 @@ pp_status pp_submit(pp_server* s, const pp_job* job, uint64_t* job_id) {
   j->bloch.assign(job->bloch, job->bloch + 3 * cfg.n_qubits);
   j->n_layers = job->n_layers;
   j->boundary = job->symmetric_boundary;
-  job_features(cfg, job->n_layers, job->n_layer_gates, j->feat);
+  ppadm::job_features(cfg, job->n_layers, job->n_layer_gates, j->feat);
   j->reserve = job->mem_bytes ? job->mem_bytes
                               : (s->default_reserve ? s->default_reserve
                                                     : estimate_job_bytes(cfg, job->n_terms));
