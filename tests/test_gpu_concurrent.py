@@ -84,3 +84,35 @@ def test_grid_fraction_is_checked():
         assert e.value.status == 1  # PP_ERR_ARG
     pp.pp_set_grid_fraction(p.ctx, 1.0)
     p.close()
+
+
+def test_bench_step_matches_the_oracle_trajectory():
+    """The step bench.py times, through its own code: the plain and Z_32
+    propagations of the full ring workload (n=32, 20 steps, eps 1e-4, weight
+    <= 10) at the same time from two host threads on a quarter and three
+    quarters of the GPU, the merged run taking the whole GPU once the plain
+    run is done, from device-resident and from host inputs.  <O> must equal
+    the oracle's stored trajectory to 1e-10, and the live-term and update
+    counts must equal the oracle's."""
+    import json
+    import os
+    import torch
+    import bench
+    data = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ring_n32.json")))
+    wl = pi.config1_ring()
+    layers = [(pp.pack_gates(gx, gz), th) for gx, gz, th in layers_of(wl)]
+    ox, oz, oc = wl.observable.arrays()
+    dev = torch.device("cuda", 0)
+    obs_dev = (torch.from_numpy(ox.view(np.int64)).to(dev),
+               torch.from_numpy(oz.view(np.int64)).to(dev), torch.from_numpy(oc).to(dev))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    join = torch.cuda.Stream()
+    for host_inputs in (False, True):
+        vals, stats, _, _, end = bench.run_job_concurrent(pp, wl, layers, obs_dev, streams, join,
+                                                          host_inputs, 0.25)
+        end.synchronize()
+        for g, key in enumerate(("plain", "zn")):
+            gold = data[key][-1]
+            assert vals[g] == pytest.approx(gold["expect"], abs=1e-10)
+            assert stats[g]["live_terms"] == gold["terms"]
+            assert stats[g]["gate_updates"] == gold["updates"]
