@@ -22,19 +22,30 @@ PRIOR = np.array([-7.845, 0.887, 1.444, 0.703, 0.519, -0.438, -1.080, -0.338])
 MAX_BYPASS = 8
 
 
-@pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+@pytest.fixture(scope="module", params=["plain", "asan_ubsan"])
+def driver(request, tmp_path_factory):
+    """The driver built plainly, and with AddressSanitizer and
+    UndefinedBehaviorSanitizer (no recovery: an invalid access or undefined
+    behaviour ends the run with an error)."""
     if shutil.which("g++") is None:
         pytest.skip("no g++")
-    exe = str(tmp_path_factory.mktemp("admission") / "admission")
-    r = subprocess.run(["g++", "-O1", "-std=c++17", "-Wall", "-Wextra", "-Werror",
-                        os.path.join(HERE, "admission_main.cpp"), "-o", exe],
+    flags = ["-O1", "-std=c++17", "-Wall", "-Wextra", "-Werror"]
+    if request.param == "asan_ubsan":
+        flags += ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+                  "-fno-omit-frame-pointer"]
+    exe = str(tmp_path_factory.mktemp("admission_" + request.param) / "admission")
+    r = subprocess.run(["g++", *flags, os.path.join(HERE, "admission_main.cpp"), "-o", exe],
                        capture_output=True, text=True)
+    if r.returncode != 0 and request.param == "asan_ubsan":
+        pytest.skip("g++ without sanitizer runtimes: " + r.stderr.strip()[-200:])
     assert r.returncode == 0, r.stderr
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1", UBSAN_OPTIONS="print_stacktrace=1")
 
     def run(text):
-        out = subprocess.run([exe], input=text, capture_output=True, text=True, timeout=60)
+        out = subprocess.run([exe], input=text, capture_output=True, text=True, timeout=120,
+                             env=env)
         assert out.returncode == 0, out.stderr
+        assert "runtime error" not in out.stderr and "AddressSanitizer" not in out.stderr
         return [[float(v) for v in line.split()] for line in out.stdout.strip().splitlines()]
     return run
 

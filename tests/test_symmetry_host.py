@@ -53,19 +53,30 @@ def act(m, s):
     return "".join(out)
 
 
-@pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+@pytest.fixture(scope="module", params=["plain", "asan_ubsan"])
+def driver(request, tmp_path_factory):
+    """The driver built plainly, and with AddressSanitizer and
+    UndefinedBehaviorSanitizer (no recovery: an invalid access or undefined
+    behaviour ends the run with an error)."""
     if shutil.which("g++") is None:
         pytest.skip("no g++")
-    exe = str(tmp_path_factory.mktemp("symmetry") / "symmetry")
-    r = subprocess.run(["g++", "-O1", "-std=c++17", "-Wall", "-Wextra", "-Werror",
-                        os.path.join(HERE, "symmetry_main.cpp"), "-o", exe],
+    flags = ["-O1", "-std=c++17", "-Wall", "-Wextra", "-Werror"]
+    if request.param == "asan_ubsan":
+        flags += ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+                  "-fno-omit-frame-pointer"]
+    exe = str(tmp_path_factory.mktemp("symmetry_" + request.param) / "symmetry")
+    r = subprocess.run(["g++", *flags, os.path.join(HERE, "symmetry_main.cpp"), "-o", exe],
                        capture_output=True, text=True)
+    if r.returncode != 0 and request.param == "asan_ubsan":
+        pytest.skip("g++ without sanitizer runtimes: " + r.stderr.strip()[-200:])
     assert r.returncode == 0, r.stderr
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1", UBSAN_OPTIONS="print_stacktrace=1")
 
     def run(text):
-        out = subprocess.run([exe], input=text, capture_output=True, text=True, timeout=120)
+        out = subprocess.run([exe], input=text, capture_output=True, text=True, timeout=120,
+                             env=env)
         assert out.returncode == 0, out.stderr
+        assert "runtime error" not in out.stderr and "AddressSanitizer" not in out.stderr
         return out.stdout.strip().splitlines()
     return run
 
@@ -125,7 +136,8 @@ def test_multiset_invariance_equals_brute_force(driver, group, n):
             s = "".join(rng.choice(list("IXYZ"), size=n))
             angle = float(rng.choice([0.1, 0.25, -0.7]))
             gates += [(t, angle) for t in sorted({act(m, s) for m in els})]
-        variants = [gates, gates[1:], gates + [gates[0]], gates + [("".join(rng.choice(list("XYZ"), size=n)), 0.1)]]
+        extra = ("".join(rng.choice(list("XYZ"), size=n)), 0.1)
+        variants = [gates, gates[1:], gates + [gates[0]], gates + [extra]]
         k = int(rng.integers(len(gates)))
         variants.append(gates[:k] + [(gates[k][0], gates[k][1] + 1.0)] + gates[k + 1:])
         for v in variants:
