@@ -43,6 +43,18 @@ METRIC = "pauli_term_gate_updates_per_s"
 UNIT = "updates/s"
 KEY_BYTES = 16   # one uint64 X word + one uint64 Z word (n = 32)
 COEF_BYTES = 8   # FP64
+# per live anticommuting term: its coefficient read and rescaled (2C), the
+# child's key and coefficient written (K + C), and one insert: a key compared
+# and one index slot (K + C)
+BYTES_PER_ANTICOMMUTING = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
+
+
+def algorithmic_bytes(updates, skipped_updates, anticommuting):
+    """The layer kernel's algorithmic bytes: the key of every live term
+    entering a scanned gate, plus BYTES_PER_ANTICOMMUTING per live
+    anticommuting term.  Updates in gates the occupancy test skipped move no
+    bytes (every string commutes with the gate and nothing is read)."""
+    return KEY_BYTES * (updates - skipped_updates) + BYTES_PER_ANTICOMMUTING * anticommuting
 # DRAM bytes (read + write) per algorithmic byte of layer_kernel<1>, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the last layer
 # of the Z_32-merged job, taken with the kernel sources whose digest is
@@ -180,7 +192,6 @@ def trace_layers(args):
     ox, oz, oc = wl.observable.arrays()
     hbm, kind = peaks()
     stream = torch.cuda.Stream()
-    per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
     with torch.cuda.stream(stream):
         for label, group in (("plain", 0), ("Z32", 1)):
             cfg = pp.pp_config_default(n_qubits=32, symmetry=group, coeff_eps=wl.eps,
@@ -200,7 +211,7 @@ def trace_layers(args):
                 skip = st["skipped_updates"] - prev["skipped_updates"]
                 ac = st["anticommuting_terms"] - prev["anticommuting_terms"]
                 kms = st["gate_kernel_ms"] - prev["gate_kernel_ms"]
-                alg = KEY_BYTES * (upd - skip) + per_ac * ac
+                alg = algorithmic_bytes(upd, skip, ac)
                 gbs = alg / (kms / 1e3) / 1e9 if kms > 0 else None
                 print(json.dumps({"job": label, "layer": k, "live_terms": st["live_terms"],
                                   "stored_terms": st["stored_terms"], "gate_updates": upd,
@@ -378,10 +389,9 @@ def bench_ours(args):
                                                                       dev)
     upd_per_rank = upd / args.steps  # one job's updates (the same on every rank)
     hbm, peak_kind = peaks()
-    per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
     # gates the occupancy test skipped read nothing: their updates count in the
     # metric (every string is processed: it commutes) but add no bytes
-    bytes_alg = KEY_BYTES * (pupd - skipped) + per_ac * ac
+    bytes_alg = algorithmic_bytes(pupd, skipped, ac)
     achieved = bytes_alg / (gate_ms / 1e3) / 1e9 if gate_ms > 0 else None
     gates_per_job = len(GROUPS[args.only]) * sum(len(l[1]) for l in layers)
     h2d = len(GROUPS[args.only]) * (ox.nbytes + oz.nbytes + oc.nbytes + wl.state.bloch.nbytes +
@@ -530,11 +540,10 @@ def profile_layer(args):
             upd = after["gate_updates"] - before["gate_updates"]
             skip = after["skipped_updates"] - before["skipped_updates"]
             ac = after["anticommuting_terms"] - before["anticommuting_terms"]
-            per_ac = 2 * COEF_BYTES + KEY_BYTES + COEF_BYTES + KEY_BYTES + COEF_BYTES
             # the roofline's model: updates in gates the occupancy test skipped move no bytes
             print(json.dumps({"profile_layer": k, "updates": upd, "skipped_updates": skip,
                               "anticommuting_terms": ac,
-                              "algorithmic_bytes": KEY_BYTES * (upd - skip) + per_ac * ac,
+                              "algorithmic_bytes": algorithmic_bytes(upd, skip, ac),
                               "layer_kernel_ms": after["gate_kernel_ms"] - before["gate_kernel_ms"],
                               "launches": after["gate_kernels_timed"] - before["gate_kernels_timed"],
                               "live_terms": after["live_terms"]}), flush=True)
