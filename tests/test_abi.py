@@ -54,7 +54,12 @@ def test_config_default(lib):
                                     dict(symmetry=4), dict(symmetry=1 | (2 << 8)), dict(coef_type=2),
                                     dict(coeff_eps=-1.0), dict(noise_mode=7),
                                     dict(batch=4, noise_mode=2, noise_p=0.1),
-                                    dict(coef_type=1, noise_mode=2, noise_p=0.1)])
+                                    dict(coef_type=1, noise_mode=2, noise_p=0.1),
+                                    dict(coeff_eps=float("nan")), dict(noise_mode=1, noise_p=-0.1),
+                                    dict(noise_mode=2, noise_p=float("nan")), dict(merge_method=2),
+                                    dict(wait_limit=-1), dict(room_factor=-1.0),
+                                    dict(room_factor=float("nan")), dict(room_factor=float("inf")),
+                                    dict(block_threads=512), dict(block_threads=-256)])
 def test_create_rejects_bad_config_without_gpu(lib, fields):
     cfg = pp.pp_config_default(n_qubits=8)
     for field, value in fields.items():
