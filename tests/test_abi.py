@@ -157,3 +157,30 @@ def test_binding_argument_counts_match_the_prototypes():
         a = args.strip()
         arity = 0 if a in ("", "void") else len(a.split(","))
         assert arity == len(pp._SIGS[name]), name
+
+
+def test_server_calls_validate_arguments(lib):
+    h = ctypes.c_void_p()
+    for slots, budget in ((0, 1 << 30), (257, 1 << 30), (4, 0)):
+        assert lib.pp_server_create(slots, budget, 0, ctypes.byref(h)) == 1  # PP_ERR_ARG
+        assert h.value is None
+    assert lib.pp_server_create(4, 1 << 30, 0, None) == 1
+    job, jid = pp.pp_job(), ctypes.c_uint64()
+    assert lib.pp_submit(None, ctypes.byref(job), ctypes.byref(jid)) == 1
+    assert lib.pp_last_error().decode() != ""
+
+
+def test_calls_that_need_a_gpu_fail_loudly_without_one(lib):
+    """Without a GPU a context or a server is not created: the call returns
+    PP_ERR_CUDA with a message (no CPU fallback, no crash)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.pp_server_create(2, 1 << 30, 0, ctypes.byref(h)) == 5  # PP_ERR_CUDA
+    assert h.value is None and lib.pp_last_error().decode() != ""
+    cfg = pp.pp_config_default(n_qubits=8)
+    x, z = (ctypes.c_uint64 * 1)(0), (ctypes.c_uint64 * 1)(1)
+    c = (ctypes.c_double * 1)(1.0)
+    assert lib.pp_create(ctypes.byref(cfg), 1, x, z, c, ctypes.byref(h)) == 5
+    assert h.value is None and lib.pp_last_error().decode() != ""
