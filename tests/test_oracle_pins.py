@@ -522,6 +522,32 @@ def test_batched_truncation_keeps_a_term_if_any_column_is_large(oracle_lib):
     assert got == {"ZII": (1e-4, 2e-2), "IYI": (0.5, 0.5)}
 
 
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_ising_counts_saturate_at_the_orbit_numbers(oracle_lib, n):
+    """The periodic Ising example (Fig. 1 and its caption, Example "Translation
+    symmetry Z_n"): without truncation, propagating Z at site ceil(n/2) through
+    the Trotter layers fills the whole traceless operator space, so the plain
+    count saturates at 4^n - 1 strings and the merged count at the number of
+    Z_n orbits of non-identity strings, (4^n + 4(n-1))/n - 1 for prime n
+    (Burnside).  At every layer the merged count is at most the plain one,
+    and below it from the second layer on."""
+    wl = pi.config1_ring(n=n, steps=7, theta_j=0.37, theta_x=0.81, theta_z=0.53, eps=0.0,
+                         max_weight=-1)
+    x, z = pi.to_masks([pi.pauli(n, {(n + 1) // 2 - 1: "Z"})], n)
+    counts = {}
+    for group in (0, 1):
+        st = oracle_lib.OracleState(n, x, z, np.array([1.0]), group=group)
+        counts[group] = []
+        for layer in reversed(range(len(wl.circuit.layers))):
+            gx, gz, th = wl.circuit.gate_arrays(layer)
+            st.apply_layer(gx, gz, th, group=group)
+            counts[group].append(len(st))
+    assert counts[0][-1] == 4 ** n - 1
+    assert counts[1][-1] == (4 ** n + 4 * (n - 1)) // n - 1
+    assert all(m <= p for m, p in zip(counts[1], counts[0]))
+    assert all(m < p for m, p in zip(counts[1][1:], counts[0][1:]))
+
+
 # -------------------------- ingest, the update count, batched merging
 
 def test_ingest_accumulates_repeated_strings(oracle_lib):
