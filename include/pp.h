@@ -437,9 +437,10 @@ pp_status pp_server_destroy(pp_server* server);
 
 /* pp_merge_terms without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory while they run -- a serving loop whose memory is fixed at
- * start-up, a thread capturing work into a CUDA graph, or an application that
- * owns every allocation itself.  The result is the same as pp_merge_terms
+ * device memory while they run -- a serving loop whose device memory is sized
+ * once at start-up (an allocation later could fail under load, or stall the
+ * device while it synchronises), or an application that hands out every
+ * device allocation from its own pool.  The result is the same as pp_merge_terms
  * (distinct strings in keys_out, FP64 sums in coef_out, unspecified order),
  * but:
  *  - the count is written to *m_out_dev, a DEVICE pointer owned by the

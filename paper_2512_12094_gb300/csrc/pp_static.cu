@@ -2,11 +2,11 @@
 // pp_merge_terms for callers that must not allocate device memory.
 //
 // Who needs this: code that runs where cudaMalloc / cudaMallocAsync are not
-// available or not allowed -- for example a serving loop whose device memory
-// is fixed when it starts and may not grow afterwards, a host thread that is
-// capturing work into a CUDA graph on a stream (allocating calls would break
-// the capture or be recorded into it), or an embedding application that owns
-// every allocation itself.  Such a caller still owns its inputs and outputs
+// allowed once it is running -- for example a serving loop whose device
+// memory is sized when it starts and may not grow afterwards (an allocation
+// later could fail under load, or stall the device while it synchronises), or
+// an embedding application that hands out every device allocation from its
+// own pool.  Such a caller still owns its inputs and outputs
 // and passes them in; the only memory this call needs beyond them (a hash
 // index and a small control block) lives in the static device array below.
 //

@@ -1,8 +1,9 @@
 """The allocation-free merge entry point agrees with the allocating one.
 
 pp_merge_terms_noalloc serves callers that may not allocate device memory
-while they run (a serving loop with memory fixed at start-up, a thread that is
-capturing a CUDA graph, an application that owns all allocations): its
+while they run: a serving loop whose device memory is sized once at start-up
+(an allocation later could fail under load or stall the device), or an
+application that hands out every device allocation from its own pool.  Its
 scratch lives in a static device array inside the library.  Here it is called
 through the C ABI twice in a row, on different inputs, and each result is
 compared with pp_merge_terms on the same input.  The second call also checks
@@ -75,11 +76,10 @@ def test_noalloc_merge_rejects_oversized_input():
     assert "524288" in str(e.value)
 
 
-def test_noalloc_merge_allocates_nothing_and_replays_in_a_cuda_graph():
-    """Free device memory is the same before and after the call, and the call
-    (after a first call on the device, which looks up the scratch address) can
-    be captured into a CUDA graph in global capture mode and replayed on new
-    inputs: each replay matches pp_merge_terms on those inputs."""
+def test_noalloc_merge_allocates_nothing():
+    """Free device memory is the same before and after a call (after a first
+    call on the device, which looks up the scratch address), and that call's
+    result matches pp_merge_terms on the same input."""
     import torch
     n, group, m = 24, 1, 4000
     keys, coef, W = _keys(n, m, 11)
@@ -97,20 +97,11 @@ def test_noalloc_merge_allocates_nothing_and_replays_in_a_cuda_graph():
     stream.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream, capture_error_mode="global"):
-        pp.pp_merge_terms_noalloc(n, group, m, d_k, d_c, out_k, out_c, m_dev, stream)
-    for seed in (12, 13):
-        keys2, coef2, _ = _keys(n, m, seed)
-        d_k.copy_(torch.from_numpy(keys2.view(np.int64)))
-        d_c.copy_(torch.from_numpy(coef2))
-        graph.replay()
-        torch.cuda.synchronize()
-        ref_k, ref_c = torch.empty_like(d_k), torch.empty_like(d_c)
-        m_ref = pp.pp_merge_terms(n, group, m, d_k, d_c, ref_k, ref_c)
-        m_got = int(m_dev.cpu()[0])
-        assert m_got == m_ref
-        got = _as_dict(out_k[:m_got].cpu().numpy().view(np.uint64), out_c[:m_got].cpu().numpy())
-        want = _as_dict(ref_k[:m_ref].cpu().numpy().view(np.uint64), ref_c[:m_ref].cpu().numpy())
-        assert set(got) == set(want)
-        assert max(abs(got[k] - want[k]) for k in want) < 1e-12
+    ref_k, ref_c = torch.empty_like(d_k), torch.empty_like(d_c)
+    m_ref = pp.pp_merge_terms(n, group, m, d_k, d_c, ref_k, ref_c)
+    m_got = int(m_dev.cpu()[0])
+    assert m_got == m_ref
+    got = _as_dict(out_k[:m_got].cpu().numpy().view(np.uint64), out_c[:m_got].cpu().numpy())
+    want = _as_dict(ref_k[:m_ref].cpu().numpy().view(np.uint64), ref_c[:m_ref].cpu().numpy())
+    assert set(got) == set(want)
+    assert max(abs(got[k] - want[k]) for k in want) < 1e-12
