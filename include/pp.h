@@ -243,8 +243,9 @@ pp_status pp_apply_layer(pp_ctx* ctx, int n_gates, const pp_pauli* gates, const 
                          int symmetric_boundary);
 
 /* Replace every string by its orbit representative under the context's
- * group (Algorithm 2 line "argmin int(T^j s)"; Algorithm 3 line "Z^{nZ}
- * Y^{nY} X^{nX}") without accumulating: the table may then hold duplicates
+ * group (for Z_n the translation with the lowest digit integer, Algorithm 2;
+ * for S_n the layout Z^{nZ} Y^{nY} X^{nX} on the lowest qubits, Algorithm 3)
+ * without accumulating: the table may then hold duplicates
  * until pp_merge.  Any later call that needs unique strings merges first.
  * Errors: PP_ERR_STATE when the context has no symmetry. */
 pp_status pp_canonicalize(pp_ctx* ctx);
