@@ -165,6 +165,63 @@ MUTANTS = [
     ("batched_merge_overwrites",
      [("for (int b = 0; b < st->B; ++b) row[b] += kv.second[b];",
        "for (int b = 0; b < st->B; ++b) row[b] = kv.second[b];", 1, 0)]),
+    # --- further mistakes: argmax for argmin, truncation skipped after a merge,
+    # the second mask word, single-site phases, other weights and lookups
+    ("representative_is_the_largest",
+     [("if (a[q] != b[q]) return (uint8_t)a[q] < (uint8_t)b[q];",
+       "if (a[q] != b[q]) return (uint8_t)a[q] > (uint8_t)b[q];", 1, 0)]),
+    ("merge_not_truncated",
+     [("  symmetry_merge(st, group);\n  truncate_all(st, eps, wmax);\n  return 0;",
+       "  symmetry_merge(st, group);\n  return 0;", 1, 0)]),
+    ("ingest_not_truncated",
+     [("  if (group != 0) symmetry_merge(st, group);\n  truncate_all(st, eps, wmax);\n  return st;",
+       "  if (group != 0) symmetry_merge(st, group);\n  return st;", 1, 0)]),
+    ("batched_merge_not_truncated",
+     [("    bmerge(st, group);\n    btruncate(st, eps, wmax);\n  }",
+       "    bmerge(st, group);\n  }", 1, 0)]),
+    ("layer_noise_as_power_of_one_minus_gamma",
+     [("std::exp(-gamma * (double)weight(kv.first))", "std::pow(1.0 - gamma, (double)weight(kv.first))", 1, 0)]),
+    ("batched_expect_uses_first_column",
+     [("out[b] += kv.second[b] * ov;", "out[b] += kv.second[0] * ov;", 1, 0)]),
+    ("second_mask_word_ignored",
+     [("int xb = (x[q / 64] >> (q % 64)) & 1;\n    int zb = (z[q / 64] >> (q % 64)) & 1;",
+       "int xb = (x[0] >> (q % 64)) & 1;\n    int zb = (z[0] >> (q % 64)) & 1;", 1, 0)]),
+    ("phase_from_last_site_only",
+     [("      phase += pr.phase;\n    }\n    // P Q", "      phase = pr.phase;\n    }\n    // P Q", 1, 0)]),
+    ("weight_counts_only_z",
+     [("for (char ch : s) w += (ch != 0);", "for (char ch : s) w += (ch == 3);", 1, 0)]),
+    ("sn_table_lookup_y_and_z_swapped",
+     [("return st->sn_table[((size_t)nx * S + ny) * S + nz];",
+       "return st->sn_table[((size_t)nx * S + nz) * S + ny];", 1, 0)]),
+    ("element_overlap_divided_by_n",
+     [("return acc / (double)els.size();", "return acc / (double)st->n;", 1, 0)]),
+    ("zn_overlap_skips_identity_translation",
+     [("for (int j = 0; j < st->n; ++j) acc += product_overlap(translate(s, j), bloch);",
+       "for (int j = 1; j < st->n; ++j) acc += product_overlap(translate(s, j), bloch);", 1, 0)]),
+    ("sn_overlap_drops_identity_sites",
+     [("if (i > 0) v += (double)i * bloch_value(bloch, k, 0) * next[at(x, y, z)];\n", "", 1, 0)]),
+    ("merge_always_by_translations",
+     [("merged[canonical(kv.first, group)] += kv.second;", "merged[canonical(kv.first, 1)] += kv.second;", 1, 0)]),
+    ("batched_merge_always_by_translations",
+     [("auto& row = merged[canonical(kv.first, group)];", "auto& row = merged[canonical(kv.first, 1)];", 1, 0)]),
+    ("letters_y_written_without_x",
+     [("if (l == 1 || l == 2) x[q / 64]", "if (l == 1) x[q / 64]", 1, 0)]),
+    ("batched_commuting_row_dropped",
+     [("      for (int b = 0; b < B; ++b) r[b] += d[b];\n      continue;",
+       "      continue;", 1, 0)]),
+    ("batched_cos_on_child",
+     [("for (int b = 0; b < B; ++b) rr[b] += sign * (s[b] * d[b]);",
+       "for (int b = 0; b < B; ++b) rr[b] += sign * (c[b] * d[b]);", 1, 0)]),
+    ("torus_rows_not_translated",
+     [("for (int dy = 0; dy < ly; ++dy)", "for (int dy = 0; dy < 1; ++dy)", 1, 0)]),
+    ("keep_ignores_eps_sign_of_negative",
+     [("if (eps > 0.0 && !(std::fabs(c) >= eps)) return false;",
+       "if (eps > 0.0 && !(c >= eps)) return false;", 1, 0)]),
+    ("batched_keep_ignores_abs",
+     [("    if (std::fabs(v) >= eps) return true;", "    if (v >= eps) return true;", 1, 0)]),
+    ("export_second_word_into_the_first",
+     [("if (l == 1 || l == 2) x[q / 64] |=", "if (l == 1 || l == 2) x[0] |=", 1, 0),
+      ("if (l == 2 || l == 3) z[q / 64] |=", "if (l == 2 || l == 3) z[0] |=", 1, 0)]),
 ]
 
 

@@ -50,6 +50,17 @@ def test_rx_on_z_and_y(oracle_lib, theta):
     assert out["Z"] == pytest.approx(-math.sin(theta), abs=1e-15)
 
 
+@pytest.mark.parametrize("n,q", [(70, 67), (130, 129)])
+def test_rz_on_x_beyond_the_first_mask_word(oracle_lib, n, q):
+    """The same closed form on a qubit held in the second or third 64-bit
+    word of the masks: strings of more than 64 qubits take several words."""
+    theta = 0.3
+    out = _single(oracle_lib, n, pi.pauli(n, {q: "X"}), [(pi.pauli(n, {q: "Z"}), theta)])
+    assert out[pi.pauli(n, {q: "X"})] == pytest.approx(math.cos(theta), abs=1e-15)
+    assert out[pi.pauli(n, {q: "Y"})] == pytest.approx(-math.sin(theta), abs=1e-15)
+    assert len(out) == 2
+
+
 def test_commuting_gate_is_identity(oracle_lib):
     out = _single(oracle_lib, 3, "ZZI", [("ZZZ", 0.7), ("XXI", 0.4)])
     assert out == {"ZZI": 1.0}
@@ -192,7 +203,7 @@ def test_sn_representative_is_argmin_over_all_permutations(oracle_lib, n):
         assert g == best
 
 
-@pytest.mark.parametrize("n", [3, 5, 8])
+@pytest.mark.parametrize("n", [3, 5, 8, 70, 130])
 def test_zn_representative_is_argmin_and_invariant(oracle_lib, n):
     rng = np.random.default_rng(100 + n)
     strings = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(60)]
@@ -368,6 +379,33 @@ def test_truncation_threshold_and_weight(oracle_lib):
     got = dict(zip(pi.from_masks(*st.export()[:2], n), st.export()[2]))
     # |c| >= eps kept (ZIII at exactly eps), XXII below eps, ZZZZ too heavy
     assert got == {"ZIII": 1e-3, "YYYI": 0.5}
+
+
+def test_truncation_follows_the_symmetry_merge(oracle_lib):
+    """The coefficient rule applies to the operator held after a merge (Alg. 1
+    step 2b gives O~, whose coefficients are orbit sums, Eq. O-merging): on
+    n = 3 with Z_3, 0.6 ZII - 0.55 IZI + 0.3 ZZI passes eps = 0.1 term by term,
+    but ZII and IZI share an orbit whose sum 0.05 is below eps, so after a
+    layer of RZ gates (which commute with every term) and the merge only the
+    representative ZZI remains, with 0.3."""
+    n = 3
+    strings = ["ZII", "IZI", "ZZI"]
+    x, z = pi.to_masks(strings, n)
+    st = oracle_lib.OracleState(n, x, z, np.array([0.6, -0.55, 0.3]), eps=0.1)
+    assert len(st) == 3
+    layer = [(pi.pauli(n, {q: "Z"}), 0.7) for q in range(n)]
+    gx, gz, th = pi.Circuit(n, [layer]).gate_arrays(0)
+    st.apply_layer(gx, gz, th, group=1)
+    got = dict(zip(pi.from_masks(*st.export()[:2], n), st.export()[2]))
+    assert got == {"ZZI": 0.3}
+    # batched rows: a merged row is kept iff some column reaches eps
+    rows = np.array([[0.6, 0.5], [-0.55, -0.45], [0.3, 0.01]])
+    bst = oracle_lib.BatchedOracleState(n, 2, x, z, rows, eps=0.1)
+    assert len(bst) == 3
+    bst.apply_layer(gx, gz, np.repeat(th[:, None], 2, axis=1), group=1)
+    bx, bz, bc = bst.export()
+    assert pi.from_masks(bx, bz, n) == ["ZZI"]
+    assert bc.tolist() == [[0.3, 0.01]]
 
 
 def test_truncation_never_drops_zero_when_off(oracle_lib):
@@ -642,6 +680,32 @@ def test_batched_symmetry_merge_keeps_every_column_exact(oracle_lib):
         assert got[b] == pytest.approx(ref, abs=1e-12)
     assert len(set(np.round(got, 9))) == B
     assert len(merged) < len(plain)
+
+
+def test_batched_sn_merge_keeps_every_column_exact(oracle_lib):
+    """Batched rows merged by S_n representatives after every layer of the
+    permutation-invariant layer (all-pairs ZZ, then RX and RZ on every qubit)
+    with different angles per column: without truncation every column's <O>
+    is the state-vector value for its own angles (Theorem 1; from the Neel
+    state, which is not S_n-invariant, through the orbit-averaged overlap),
+    and the merged table holds at most C(n+3, 3) representatives."""
+    n, B, L = 5, 3, 2
+    cols = [(0.37, 0.81, -0.45), (-0.6, 0.2, 1.1), (1.3, -0.9, 0.25)]
+    layers = [_symmetric_sn_layer(n, *a) for a in cols]
+    gx, gz, _ = pi.Circuit(n, [layers[0]]).gate_arrays(0)
+    th = np.array([[layers[b][g][1] for b in range(B)] for g in range(len(layers[0]))])
+    obs = pi.mean_z(n)
+    x, z, c = obs.arrays()
+    state = pi.neel_state(n)
+    merged = oracle_lib.BatchedOracleState(n, B, x, z, np.repeat(c[:, None], B, axis=1), group=2)
+    for _ in range(L):
+        merged.apply_layer(gx, gz, th, group=2)
+    got = merged.expect(state.bloch, 2)
+    for b in range(B):
+        ref = sv.statevector_expectations([layers[b]] * L, obs.terms, state.bloch)[-1]
+        assert got[b] == pytest.approx(ref, abs=1e-12)
+    assert len(set(np.round(got, 9))) == B
+    assert len(merged) <= math.comb(n + 3, 3)
 
 
 # ------------------------------------------ the stored expected values
