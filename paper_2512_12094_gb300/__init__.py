@@ -57,8 +57,8 @@ def _nvcc():
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libpp.so in-tree for sm_103a (objects in parallel, then link)."""
     srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
-    deps = srcs + [os.path.join(_CSRC, "pp_internal.h"), os.path.join(_CSRC, "pp_device.cuh"),
-                   os.path.join(_ROOT, "include", "pp.h")]
+    deps = srcs + [os.path.join(_CSRC, h) for h in sorted(os.listdir(_CSRC))
+                   if h.endswith((".h", ".cuh"))] + [os.path.join(_ROOT, "include", "pp.h")]
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(d) for d in deps)):
         return _LIB
