@@ -481,6 +481,30 @@ def result_summary(vals, stats, only):
     return out
 
 
+def host_cpu():
+    """The host the CPU baseline ran on: logical CPUs, architecture and the
+    CPU model as /proc/cpuinfo names it (x86: "model name"; Arm: the
+    implementer and part numbers), for the baseline's record."""
+    import platform
+    info = {"nproc": os.cpu_count(), "arch": platform.machine()}
+    try:
+        with open("/proc/cpuinfo") as f:
+            fields = {}
+            for ln in f:
+                k, _, v = ln.partition(":")
+                k, v = k.strip(), v.strip()
+                if k and v and k not in fields:
+                    fields[k] = v
+        if "model name" in fields:
+            info["model"] = fields["model name"]
+        elif "CPU part" in fields:
+            info["model"] = "implementer %s part %s" % (fields.get("CPU implementer", "?"),
+                                                        fields["CPU part"])
+    except OSError:
+        pass
+    return info
+
+
 def cpu_baseline(seconds=20.0):
     """The CPU oracle, as it stands, on a bounded prefix of the same workload:
     plain and Z_32-merged propagation, layer by layer, each run stopped once
@@ -508,7 +532,7 @@ def cpu_baseline(seconds=20.0):
     return {"value": total_upd / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "first %d (plain) and %d (Z_32) of 20 Trotter steps of the job, "
                       "%.1f s CPU, %.3g updates" % (done[0], done[1], total_t, total_upd),
-            "seconds": total_t}
+            "seconds": total_t, "host": host_cpu()}
 
 
 def profile_layer(args):
@@ -1084,7 +1108,7 @@ def bench_reference(args):
             "config": {"workload": WORKLOAD,
                        "step": "a bounded prefix of the job (CPU time per step fixed)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+                             "sample": vals[-1]["sample"], "host": vals[-1]["host"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -77,3 +77,9 @@ def test_served_results_against_alone():
     # a sample: job k of the stream against the k-th job run alone
     assert bench.served_max_diff(res, alone[:2], [0, 1]) == 2.0 ** -52
     assert bench.served_max_diff(res[2:], alone[2:], None) is None  # failed jobs are not compared
+
+
+def test_host_cpu_record():
+    h = bench.host_cpu()
+    assert h["nproc"] == os.cpu_count() and h["arch"]
+    assert "model" not in h or isinstance(h["model"], str)
