@@ -20,7 +20,10 @@
  *   with digits I=0, X=1, Y=2, Z=3 and qubit q carrying weight 4^q.
  * Truncation (Sec. "Numerical examples", coefficient truncation): after every
  *   gate and every merge a term is kept iff |c| >= coeff_eps (when
- *   coeff_eps > 0) and its Pauli weight is <= max_weight (when >= 0).
+ *   coeff_eps > 0) and its Pauli weight is <= max_weight (when >= 0).  After
+ *   a symmetry merge c is the merged coefficient, the sum over the members of
+ *   the orbit (Eq. O-merging), so a representative can survive although each
+ *   member alone would not, and the reverse when the members cancel.
  * Errors: every call returns a pp_status; no C++ exception crosses the ABI.
  *   pp_last_error() gives a message for the calling thread's last failure.
  * Threads: a pp_ctx is used by one host thread at a time.
