@@ -793,7 +793,8 @@ pp_status create_common(const pp_config* cfg, int64_t n_terms, const uint64_t* x
   };
   {
     int dev = 0, coop = 0;
-    cudaGetDevice(&dev);
+    const cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cleanup(cuda_fail(de, "no usable CUDA device (cudaGetDevice)"));
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (coop && c->batched) {
       c->layer_bps = layer_batched_blocks_per_sm(c->W, c->f32);

@@ -184,3 +184,26 @@ def test_calls_that_need_a_gpu_fail_loudly_without_one(lib):
     c = (ctypes.c_double * 1)(1.0)
     assert lib.pp_create(ctypes.byref(cfg), 1, x, z, c, ctypes.byref(h)) == 5
     assert h.value is None and lib.pp_last_error().decode() != ""
+
+
+def test_plain_c_program_builds_and_runs_against_the_library(lib, tmp_path):
+    """tests/abi_example.c uses the library from C99 alone (create, apply
+    three Z_n-merged layers, expect, destroy).  It compiles warning-free
+    against include/pp.h and links against libpp.so; without a GPU it stops
+    at pp_create with PP_ERR_CUDA and a message, with one it prints <O>."""
+    import torch
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pkg = os.path.dirname(os.path.abspath(pp.__file__))
+    exe = tmp_path / "abi_example"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_example.c"), "-L", pkg, "-lpp",
+                    "-Wl,-rpath," + pkg, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    if torch.cuda.is_available():
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.startswith("<O> = ")
+    else:
+        assert r.returncode == 2, (r.returncode, r.stdout, r.stderr)
+        assert r.stderr.startswith("pp_create failed: status 5: ") and len(r.stderr) > 30
